@@ -1,0 +1,216 @@
+/*
+ * libmm -- GB300-native magnification maps for gravitational microlensing:
+ * fast-multipole ray deflection plus inverse polygon mapping (Weisenbach
+ * 2025, "Rootin' Tootin' Efficient Ray Shootin'").
+ *
+ * A map is the pixel-averaged magnification of a square source-plane region
+ * for the lens equation of Sec. 2.2 (complex form)
+ *
+ *     w = (1 - kappa) z + gamma conj(z) - alpha_star(z) - alpha_s(z),
+ *     alpha_star(z) = sum_i m_i / (conj(z) - conj(z_i))         (theta_star = 1)
+ *     alpha_s(z)    = -kappa_star z                (circular sheet, Sec. 3.1)
+ *
+ * built by shooting a regular grid of rays from the image-plane region of
+ * Sec. 2.3 / App. A, splitting each grid cell into two triangles and
+ * apportioning each mapped triangle's area exactly among the pixels it covers
+ * (Sec. 3.2).  The deflection uses the quadtree fast multipole method of
+ * Sec. 3.3 and App. C.
+ *
+ * Conventions for every call:
+ *   - All functions return mm_status; no C++ exception crosses this ABI.
+ *     mm_last_error() returns a thread-local message for the last failure.
+ *   - Positions are interleaved (x, y) doubles; units are Einstein radii of a
+ *     unit mass (theta_star = 1).
+ *   - A map is npix*npix values, row-major, row index = y pixel; pixel (px, py)
+ *     covers [c_x - L + px*d, c_x - L + (px+1)*d) x (same in y), with
+ *     L = half_length, d = 2L/npix, c = map centre.
+ *   - A handle owns all of its device memory and is used by one host thread
+ *     at a time.  Different handles may run concurrently on different streams.
+ *   - "stream" arguments are cudaStream_t values passed as void*; NULL is the
+ *     legacy default stream.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_map mm_map; /* opaque handle */
+
+typedef enum {
+  MM_OK = 0,
+  MM_EINVAL = 1,   /* invalid argument; nothing was changed */
+  MM_ENOMEM = 2,   /* device or host allocation failed */
+  MM_ECUDA = 3,    /* a CUDA call failed (message in mm_last_error) */
+  MM_ETIMEOUT = 4, /* a bounded device-side wait gave up; handle is unusable */
+  MM_ESTATE = 5    /* call not valid in the handle's state */
+} mm_status;
+
+typedef enum {
+  MM_FMM_FP32 = 0,  /* FMM deflection, FP32 per ray, FP64 expansions (default) */
+  MM_PLAIN_FP64 = 1 /* direct sum over every star in FP64 (no tree) */
+} mm_mode;
+
+/* Options; a zero-initialised struct (or NULL) selects the defaults. */
+typedef struct {
+  int32_t mode;             /* mm_mode */
+  int32_t time_stages;      /* 1: record CUDA events around each stage of
+                               mm_run; read them with mm_get_stats */
+  double img_half[2];       /* > 0: explicit half-widths of the image-plane
+                               shooting region (else Sec. 2.3 / App. A) */
+  int64_t ray_grid[2];      /* >= 2: explicit rays per axis spanning exactly
+                               the region (else spacing d/sqrt(rays_per_pixel),
+                               square cells, grid centred on the region) */
+  double flux_fraction_f;   /* App. A flux fraction beyond the border; 0 -> 1e-3 */
+  double center_y[2];       /* map centre in the source plane (Sec. 2.3) */
+  int64_t row_begin;        /* shoot only cell rows [row_begin, row_end) of the */
+  int64_t row_end;          /*   ray grid; both 0 -> every row */
+  int32_t rows_per_item;    /* rows of cells per warp work item, 1..4096; 0 -> 64 */
+  int32_t reserved;
+} mm_options;
+
+/* Every derived scalar of a run (host-side numbers; no GPU needed). */
+typedef struct {
+  double kappa, gamma, smooth_fraction;
+  double kappa_star;        /* (1 - s) kappa, Sec. 2.1 */
+  double a1, a2;            /* 1 - kappa + gamma, 1 - kappa - gamma */
+  double mu_macro;          /* 1 / ((1-kappa)^2 - gamma^2), Sec. 3.1 */
+  double mean_m, m2_over_m; /* <m>, <m^2>/<m> of the given stars */
+  double flux_fraction_f;
+  double r_border;          /* sqrt(kappa_star <m^2> / (f <m>)), App. A */
+  double half_length;
+  int32_t npix;
+  int32_t pad0;
+  double delta;             /* pixel side */
+  double center_y[2];
+  double img_center[2];     /* centre of the shooting region, Sec. 2.3 */
+  double img_half[2];       /* half-widths of the shooting region */
+  int64_t n[2];             /* rays (grid vertices) per axis */
+  double h[2];              /* ray spacing per axis */
+  double x0[2];             /* image-plane position of vertex (0, 0) */
+} mm_params;
+
+typedef struct {
+  mm_params params;
+  int32_t mode;
+  int32_t fmm_order;        /* expansion order p actually used */
+  int32_t leaf_size;        /* maximum stars used directly (App. C.1), default 32 */
+  int32_t depth;            /* deepest tree level */
+  int64_t n_stars;
+  int64_t nodes;            /* tree nodes over all levels */
+  int64_t leaves;           /* leaves over all levels */
+  int64_t active_leaves;    /* leaves containing ray-grid vertices */
+  double root_half_length;
+  double min_leaf_half_length; /* smallest half-length of an active leaf */
+  double mean_near_stars;   /* mean near-field (direct) stars per active-leaf
+                               vertex, weighted by vertices */
+  int64_t rays;             /* grid vertices shot by mm_run (band included) */
+  int64_t cells;            /* grid cells mapped by mm_run */
+  int64_t triangles_dropped;/* zero-area or non-finite triangles (last run) */
+  int64_t triangles_clipped;/* triangles spanning more than one pixel of the map */
+  int64_t triangles_quad;   /*   of which within a 2 x 2 pixel box (closed form) */
+  int64_t triangles_strip;  /*   of which clipped by column/row strips */
+  int64_t triangles_span;   /*   of which walked row by row by a whole warp */
+  int64_t kernel_launches;  /* library kernels launched by the last run (CUB's
+                               sort/scan kernels and memsets not counted) */
+  /* stage times of the last mm_run in ms (time_stages = 1), else -1 */
+  double ms_tree, ms_expansions, ms_shoot, ms_normalize, ms_total;
+} mm_stats;
+
+/*
+ * Derive the run's scalars without touching a GPU: kappa_star (Sec. 2.1),
+ * mu_macro (Sec. 3.1), the border r (App. A), the shooting region (Sec. 2.3)
+ * and the ray grid (Sec. 3.2 / Table 1 caption).  masses: host, n_stars
+ * values (may be NULL when n_stars == 0).  Returns MM_EINVAL for the
+ * arguments mm_create rejects.
+ */
+mm_status mm_derive_params(double kappa_tot, double shear, double smooth_fraction,
+                           int64_t n_stars, const double *masses,
+                           double half_length, int32_t npix, double rays_per_pixel,
+                           const mm_options *opt, mm_params *out);
+
+/*
+ * Create a map handle.  Copies the stars to the device (the caller may free
+ * masses/pos_xy on return), derives every parameter, builds the quadtree once
+ * to size its workspace, and allocates all device memory the handle needs.
+ *
+ *   kappa_tot, shear, smooth_fraction: kappa, gamma, s of Sec. 2.1;
+ *     kappa_star = (1 - s) kappa.
+ *   n_stars, masses[n_stars], pos_xy[2*n_stars]: host arrays, masses > 0.
+ *   half_length, npix: square map of side 2*half_length, npix pixels a side.
+ *   rays_per_pixel: rays per pixel in the absence of lensing (Table 1
+ *     caption); ignored when opt->ray_grid is given.
+ *   fmm_order: expansion order p (App. C.3); 0 picks
+ *     p > log2(<m^2>/<m> / (L eps)) with eps = d/10 and L the smallest active
+ *     leaf half-length; accepted range [0, 64].
+ *   leaf_size: maximum number of stars in a node and its neighbours used
+ *     directly (Sec. 3.3); 0 -> 32; accepted range [0, 1024].
+ *   opt: may be NULL.
+ *   out: receives the handle.
+ *
+ * Errors: MM_EINVAL for |(1-kappa)^2 - gamma^2| < 1e-12, s outside [0,1],
+ * kappa_star > 0 with no stars, masses <= 0 or non-finite positions, npix < 1,
+ * half_length <= 0, fmm_order or leaf_size out of range, a shooting region
+ * not inside the stars' bounding box (unless img_half is explicit), or a ray
+ * grid above 2^31 rays per axis; MM_ENOMEM / MM_ECUDA otherwise.
+ */
+mm_status mm_create(double kappa_tot, double shear, double smooth_fraction,
+                    int64_t n_stars, const double *masses, const double *pos_xy,
+                    double half_length, int32_t npix, double rays_per_pixel,
+                    int32_t fmm_order, int32_t leaf_size, const mm_options *opt,
+                    mm_map **out);
+
+/*
+ * Compute the map on the given stream: tree build (Morton sort, levels,
+ * interaction lists), multipole up-sweep, local down-sweep, fused ray
+ * deflection + inverse polygon mapping into a fixed-point accumulator, and
+ * normalisation to magnification.  Asynchronous: returns once enqueued.
+ * The caller synchronises the stream before reading results from the host.
+ */
+mm_status mm_run(mm_map *h, void *stream);
+
+/*
+ * Run n handles (all created in MM_FMM_FP32 mode on the current device) with
+ * one persistent deflection+mapping launch whose work queue spans every map.
+ */
+mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream);
+
+/*
+ * Copy the magnification map (npix*npix floats) into out.  on_device = 0:
+ * out is host memory (the call synchronises); 1: out is device memory and the
+ * copy is enqueued on the handle's last stream.
+ */
+mm_status mm_get_map(const mm_map *h, float *out, int32_t on_device);
+
+/*
+ * Copy the raw accumulator (npix*npix uint64): the sum over triangles of
+ * round(fraction * 2^32) per pixel.  Integer sums make it bit-identical from
+ * run to run.  Same on_device rule as mm_get_map.
+ */
+mm_status mm_get_map_fixed(const mm_map *h, uint64_t *out, int32_t on_device);
+
+/*
+ * Deflection probe: source positions w (interleaved, n points) of image-plane
+ * points z (interleaved), evaluated by the same device code the map uses.
+ * Host pointers; synchronous.  FMM mode: points must lie in the shooting
+ * region (others give NaN).  Runs the tree and expansions if mm_run has not.
+ */
+mm_status mm_shoot_points(mm_map *h, int64_t n, const double *z_xy, double *w_xy);
+
+/* Statistics and derived parameters of the handle and its last run
+ * (synchronises the handle's last stream). */
+mm_status mm_get_stats(const mm_map *h, mm_stats *out);
+
+/* Thread-local message describing the last failed call ("" if none). */
+const char *mm_last_error(void);
+
+/* Release the handle and all its device memory.  NULL is accepted. */
+void mm_destroy(mm_map *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

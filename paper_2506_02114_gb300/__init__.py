@@ -1,0 +1,269 @@
+"""GB300-native magnification maps for gravitational microlensing.
+
+Thin ctypes binding over ``libmm.so`` (declared in ``include/mm.h``): the
+functions below only marshal arguments; every step of the path runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library is missing
+or no CUDA device is present, the calls raise.
+
+Typical use::
+
+    import paper_2506_02114_gb300 as mm
+    h = mm.create(kappa, gamma, s, masses, pos, half_length, npix,
+                  rays_per_pixel=9.0, fmm_order=25)
+    mm.run(h)                  # on torch's current CUDA stream
+    mu = mm.get_map(h)         # numpy (npix, npix) float32, row = y
+    mm.destroy(h)
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ETIMEOUT, MM_ESTATE = range(6)
+MM_FMM_FP32, MM_PLAIN_FP64 = 0, 1
+_STATUS = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ECUDA", 4: "MM_ETIMEOUT",
+           5: "MM_ESTATE"}
+
+
+class MMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("time_stages", ctypes.c_int32),
+                ("img_half", ctypes.c_double * 2), ("ray_grid", ctypes.c_int64 * 2),
+                ("flux_fraction_f", ctypes.c_double), ("center_y", ctypes.c_double * 2),
+                ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
+                ("rows_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("smooth_fraction", ctypes.c_double), ("kappa_star", ctypes.c_double),
+                ("a1", ctypes.c_double), ("a2", ctypes.c_double),
+                ("mu_macro", ctypes.c_double), ("mean_m", ctypes.c_double),
+                ("m2_over_m", ctypes.c_double), ("flux_fraction_f", ctypes.c_double),
+                ("r_border", ctypes.c_double), ("half_length", ctypes.c_double),
+                ("npix", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("delta", ctypes.c_double), ("center_y", ctypes.c_double * 2),
+                ("img_center", ctypes.c_double * 2), ("img_half", ctypes.c_double * 2),
+                ("n", ctypes.c_int64 * 2), ("h", ctypes.c_double * 2),
+                ("x0", ctypes.c_double * 2)]
+
+    def as_dict(self):
+        return {k: (list(getattr(self, k)) if hasattr(getattr(self, k), "__len__")
+                    else getattr(self, k)) for k, _ in self._fields_ if k != "pad0"}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("params", Params), ("mode", ctypes.c_int32), ("fmm_order", ctypes.c_int32),
+                ("leaf_size", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("n_stars", ctypes.c_int64), ("nodes", ctypes.c_int64),
+                ("leaves", ctypes.c_int64), ("active_leaves", ctypes.c_int64),
+                ("root_half_length", ctypes.c_double),
+                ("min_leaf_half_length", ctypes.c_double),
+                ("mean_near_stars", ctypes.c_double), ("rays", ctypes.c_int64),
+                ("cells", ctypes.c_int64), ("triangles_dropped", ctypes.c_int64),
+                ("triangles_clipped", ctypes.c_int64), ("triangles_quad", ctypes.c_int64),
+                ("triangles_strip", ctypes.c_int64), ("triangles_span", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("ms_tree", ctypes.c_double),
+                ("ms_expansions", ctypes.c_double), ("ms_shoot", ctypes.c_double),
+                ("ms_normalize", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "params"}
+        d["params"] = self.params.as_dict()
+        return d
+
+
+EXPORTS = ["mm_derive_params", "mm_create", "mm_run", "mm_run_batch", "mm_get_map",
+           "mm_get_map_fixed", "mm_shoot_points", "mm_get_stats", "mm_last_error",
+           "mm_destroy"]
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib(build_if_missing=True):
+    """Load libmm.so (building it when absent or stale); raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libmm.so is missing: run paper_2506_02114_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    L.mm_derive_params.restype = ctypes.c_int
+    L.mm_derive_params.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int64, _dp, ctypes.c_double, ctypes.c_int32,
+                                   ctypes.c_double, ctypes.POINTER(Options),
+                                   ctypes.POINTER(Params)]
+    L.mm_create.restype = ctypes.c_int
+    L.mm_create.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                            _dp, _dp, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                            ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Options),
+                            ctypes.POINTER(_vp)]
+    L.mm_run.restype = ctypes.c_int
+    L.mm_run.argtypes = [_vp, _vp]
+    L.mm_run_batch.restype = ctypes.c_int
+    L.mm_run_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, _vp]
+    L.mm_get_map.restype = ctypes.c_int
+    L.mm_get_map.argtypes = [_vp, _vp, ctypes.c_int32]
+    L.mm_get_map_fixed.restype = ctypes.c_int
+    L.mm_get_map_fixed.argtypes = [_vp, _vp, ctypes.c_int32]
+    L.mm_shoot_points.restype = ctypes.c_int
+    L.mm_shoot_points.argtypes = [_vp, ctypes.c_int64, _dp, _dp]
+    L.mm_get_stats.restype = ctypes.c_int
+    L.mm_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
+    L.mm_last_error.restype = ctypes.c_char_p
+    L.mm_last_error.argtypes = []
+    L.mm_destroy.restype = None
+    L.mm_destroy.argtypes = [_vp]
+    _lib = L
+    return L
+
+
+def last_error():
+    return lib().mm_last_error().decode()
+
+
+def _check(status):
+    if status != MM_OK:
+        raise MMError(status, last_error())
+
+
+def _f64(a):
+    if a is None:
+        return None
+    if hasattr(a, "detach"):  # torch tensor
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp) if a is not None and a.size else None
+
+
+def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=None,
+                 flux_fraction_f=0.0, center_y=(0.0, 0.0), row_begin=0, row_end=0,
+                 rows_per_item=0):
+    o = Options()
+    o.mode = int(mode)
+    o.time_stages = 1 if time_stages else 0
+    if img_half is not None:
+        o.img_half[0], o.img_half[1] = float(img_half[0]), float(img_half[1])
+    if ray_grid is not None:
+        o.ray_grid[0], o.ray_grid[1] = int(ray_grid[0]), int(ray_grid[1])
+    o.flux_fraction_f = float(flux_fraction_f)
+    o.center_y[0], o.center_y[1] = float(center_y[0]), float(center_y[1])
+    o.row_begin, o.row_end = int(row_begin), int(row_end)
+    o.rows_per_item = int(rows_per_item)
+    return o
+
+
+def derive_params(kappa, gamma, s, masses, half_length, npix, rays_per_pixel=0.0,
+                  **opts) -> Params:
+    """Derived scalars of a run (host only; no GPU needed)."""
+    m = _f64(masses)
+    p = Params()
+    o = make_options(**opts)
+    _check(lib().mm_derive_params(float(kappa), float(gamma), float(s), m.size, _ptr(m),
+                                  float(half_length), int(npix), float(rays_per_pixel),
+                                  ctypes.byref(o), ctypes.byref(p)))
+    return p
+
+
+class Handle:
+    """Owns an mm_map*; destroyed explicitly or when garbage collected."""
+
+    def __init__(self, ptr, npix):
+        self.ptr = ptr
+        self.npix = npix
+
+    def __del__(self):
+        try:
+            destroy(self)
+        except Exception:
+            pass
+
+
+def create(kappa, gamma, s, masses, pos_xy, half_length, npix, rays_per_pixel=0.0,
+           fmm_order=0, leaf_size=0, **opts) -> Handle:
+    m = _f64(masses)
+    pos = _f64(pos_xy)
+    if pos is not None:
+        pos = pos.reshape(-1)
+    o = make_options(**opts)
+    out = _vp()
+    _check(lib().mm_create(float(kappa), float(gamma), float(s), m.size, _ptr(m), _ptr(pos),
+                           float(half_length), int(npix), float(rays_per_pixel),
+                           int(fmm_order), int(leaf_size), ctypes.byref(o), ctypes.byref(out)))
+    return Handle(out, int(npix))
+
+
+def current_stream():
+    """torch's current CUDA stream handle (0 = legacy default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+def run(h: Handle, stream=None):
+    _check(lib().mm_run(h.ptr, _vp(current_stream() if stream is None else stream)))
+
+
+def run_batch(hs, stream=None):
+    arr = (_vp * len(hs))(*[x.ptr for x in hs])
+    _check(lib().mm_run_batch(arr, len(hs),
+                              _vp(current_stream() if stream is None else stream)))
+
+
+def get_map(h: Handle, out=None):
+    """Magnification map.  out=None: new numpy (npix, npix) float32 array.
+    out may be a torch CUDA float32 tensor with npix*npix elements."""
+    if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+        _check(lib().mm_get_map(h.ptr, _vp(out.data_ptr()), 1))
+        return out
+    a = np.empty((h.npix, h.npix), dtype=np.float32) if out is None else out
+    _check(lib().mm_get_map(h.ptr, a.ctypes.data_as(_vp), 0))
+    return a
+
+
+def get_map_fixed(h: Handle):
+    """Raw fixed-point accumulator (npix, npix) uint64: sum of round(frac*2^32)."""
+    a = np.empty((h.npix, h.npix), dtype=np.uint64)
+    _check(lib().mm_get_map_fixed(h.ptr, a.ctypes.data_as(_vp), 0))
+    return a
+
+
+def shoot_points(h: Handle, z_xy):
+    """Source positions w (n, 2) of image-plane points z (n, 2), FP64 out."""
+    z = _f64(z_xy).reshape(-1, 2)
+    w = np.empty_like(z)
+    _check(lib().mm_shoot_points(h.ptr, z.shape[0], _ptr(z), w.ctypes.data_as(_dp)))
+    return w
+
+
+def get_stats(h: Handle) -> dict:
+    s = Stats()
+    _check(lib().mm_get_stats(h.ptr, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def destroy(h: Handle):
+    if h is not None and h.ptr is not None and h.ptr.value:
+        lib().mm_destroy(h.ptr)
+        h.ptr = _vp()

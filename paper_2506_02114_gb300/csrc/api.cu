@@ -1,0 +1,1042 @@
+// libmm C ABI: parameter derivation, workspace planning and the stream-
+// ordered pipeline of a magnification map (see include/mm.h).
+//
+// mm_create derives every scalar of the run (Sec. 2.1-2.3, App. A and C.3),
+// uploads the stars, and builds the quadtree once with host read-backs of the
+// per-level node counts ("plan").  Those counts size every buffer, so mm_run
+// then rebuilds the same tree and runs the whole path with no host
+// synchronisation: Morton sort, level-by-level split/scan/children, active
+// region, P2M, M2M up-sweep, M2L + P2L + L2L down-sweep, leaf records, lookup
+// grid, fused deflection + inverse polygon mapping, big-triangle spans,
+// normalisation.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mm.h"
+#include "mm_kernels.h"
+
+#ifndef MM_SHOOT_MINB
+#define MM_SHOOT_MINB 2
+#endif
+
+using namespace mm;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_err;
+
+static mm_status fail(mm_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      if (e_ == cudaErrorMemoryAllocation) {                                            \
+        cudaGetLastError();                                                             \
+        return fail(MM_ENOMEM, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                    __LINE__);                                                          \
+      }                                                                                 \
+      return fail(MM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
+                  __LINE__);                                                            \
+    }                                                                                   \
+  } while (0)
+
+// a library kernel launch: checked and counted
+#define LCH(call)                   \
+  do {                              \
+    CK(call);                       \
+    h->launches++;                  \
+  } while (0)
+
+#define CKS(expr)                   \
+  do {                              \
+    mm_status s_ = (expr);          \
+    if (s_ != MM_OK) return s_;     \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t count, bool keep = false) {
+    if (count == 0) count = 1;
+    if (count <= n) return cudaSuccess;
+    T *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (keep && p && n) {
+      e = cudaMemcpy(q, p, n * sizeof(T), cudaMemcpyDeviceToDevice);
+      if (e != cudaSuccess) {
+        cudaFree(q);
+        return e;
+      }
+    }
+    if (p) cudaFree(p);
+    p = q;
+    n = count;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// the handle
+// ---------------------------------------------------------------------------
+
+struct mm_map {
+  int device = 0;
+  mm_params P{};
+  mm_options opt{};
+  int mode = MM_FMM_FP32;
+  int p = 0, leaf_size = 32;
+  int64_t N = 0;
+  double R0 = 1.0;
+  int64_t row_lo = 0, row_hi = 0;  // cell rows [row_lo, row_hi)
+  int rows_per_item = 64;
+  cudaStream_t plan_stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+
+  // stars
+  DBuf<double> pos_in, m_in, sx, sy, sm;
+  DBuf<uint64_t> keys_in, keys;
+  DBuf<int32_t> idx_in, idx;
+  DBuf<char> cub_tmp;
+
+  // tree
+  int depth = 0;
+  std::vector<int64_t> level_off, level_cnt;
+  int64_t n_nodes = 0;
+  DBuf<int64_t> d_level_off;
+  DBuf<uint64_t> code;
+  DBuf<int32_t> lvl, sbeg, send, first_child, split, scan;
+
+  // active region
+  DBuf<int32_t> col_cell, row_cell, node_act, leaf_flag, leaf_scan, node_active, active_list;
+  int64_t n_active = 0;
+  double min_leaf_L = 0.0;
+  int max_leaf_level = 0;
+
+  // expansions
+  DBuf<double2> MMop, MLop, LLop, mp, loc;
+  DBuf<int32_t> near_cnt, near_off;
+  int64_t n_near = 0;
+  DBuf<LeafRec> leaf;
+  DBuf<NearPos> near_pos;
+  DBuf<float> near_m;
+  DBuf<float2> coef;
+
+  // lookup grid
+  int glevel = 0, gshift = 0, gx0 = 0, gy0 = 0, gw = 1, gh = 1;
+  DBuf<int32_t> grid;
+
+  // map
+  DBuf<unsigned long long> acc, span, stat, counter, fixed_out;
+  DBuf<unsigned> err;
+  DBuf<float> map;
+  DBuf<MapDev> d_md;
+  MapDev md{};
+  DBuf<Vtx> verts;
+
+  // batch workspace (used when this handle leads an mm_run_batch call)
+  DBuf<MapDev> batch_md;
+
+  int64_t launches = 0;   // library kernels launched by the last run
+  bool prepared = false;  // tree + expansions current for the stars
+  bool ran = false;
+  bool timed_out = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool ev_recorded = false;
+};
+
+// ---------------------------------------------------------------------------
+// parameters (Sec. 2.1-2.3, 3.1, 3.2, App. A)
+// ---------------------------------------------------------------------------
+
+static mm_status derive(double kappa, double gamma, double s, int64_t n_stars,
+                        const double *masses, double half_length, int32_t npix, double rpp,
+                        const mm_options &o, mm_params &P) {
+  memset(&P, 0, sizeof P);
+  if (!std::isfinite(kappa) || !std::isfinite(gamma) || !std::isfinite(s))
+    return fail(MM_EINVAL, "kappa, gamma and s must be finite");
+  if (!(s >= 0.0 && s <= 1.0)) return fail(MM_EINVAL, "smooth_fraction %g outside [0, 1]", s);
+  if (!(half_length > 0.0)) return fail(MM_EINVAL, "half_length must be > 0");
+  if (npix < 1) return fail(MM_EINVAL, "npix must be >= 1");
+  if (n_stars < 0) return fail(MM_EINVAL, "n_stars must be >= 0");
+  if (n_stars > 0 && !masses) return fail(MM_EINVAL, "masses is NULL");
+  const double detm = (1.0 - kappa) * (1.0 - kappa) - gamma * gamma;
+  if (std::fabs(detm) < 1e-12)
+    return fail(MM_EINVAL, "|(1-kappa)^2 - gamma^2| < 1e-12: the macro model is critical");
+  P.kappa = kappa;
+  P.gamma = gamma;
+  P.smooth_fraction = s;
+  P.kappa_star = kappa * (1.0 - s);
+  P.a1 = 1.0 - kappa + gamma;
+  P.a2 = 1.0 - kappa - gamma;
+  P.mu_macro = 1.0 / detm;
+  if (P.kappa_star > 0.0 && n_stars == 0)
+    return fail(MM_EINVAL, "kappa_star > 0 needs stars");
+  double msum = 0.0, m2sum = 0.0;
+  for (int64_t i = 0; i < n_stars; i++) {
+    const double m = masses[i];
+    if (!(m > 0.0) || !std::isfinite(m)) return fail(MM_EINVAL, "mass %lld is not > 0", (long long)i);
+    msum += m;
+    m2sum += m * m;
+  }
+  P.mean_m = n_stars ? msum / (double)n_stars : 0.0;
+  P.m2_over_m = msum > 0.0 ? m2sum / msum : 0.0;
+  P.flux_fraction_f = o.flux_fraction_f > 0.0 ? o.flux_fraction_f : 1e-3;
+  // App. A: fraction f of the deflection PDF outside r
+  P.r_border = std::sqrt(P.kappa_star * P.m2_over_m / P.flux_fraction_f);
+  P.half_length = half_length;
+  P.npix = npix;
+  P.delta = 2.0 * half_length / (double)npix;
+  P.center_y[0] = o.center_y[0];
+  P.center_y[1] = o.center_y[1];
+  // Sec. 2.3: the macro image of the map, widened by the border r
+  const double a[2] = {P.a1, P.a2};
+  for (int k = 0; k < 2; k++) {
+    P.img_center[k] = P.center_y[k] / a[k];
+    P.img_half[k] = (o.img_half[0] > 0.0 && o.img_half[1] > 0.0)
+                        ? o.img_half[k]
+                        : (half_length + P.r_border) / std::fabs(a[k]);
+  }
+  const bool grid_given = o.ray_grid[0] >= 2 && o.ray_grid[1] >= 2;
+  for (int k = 0; k < 2; k++) {
+    if (grid_given) {
+      P.n[k] = o.ray_grid[k];
+      P.h[k] = 2.0 * P.img_half[k] / (double)(P.n[k] - 1);
+      P.x0[k] = P.img_center[k] - P.img_half[k];
+    } else {
+      if (!(rpp > 0.0)) return fail(MM_EINVAL, "rays_per_pixel must be > 0");
+      // rays per pixel without lensing: square cells of side delta/sqrt(rpp)
+      const double hh = P.delta / std::sqrt(rpp);
+      const double nn = std::ceil(2.0 * P.img_half[k] / hh) + 1.0;
+      if (!(nn < 2147483647.0)) return fail(MM_EINVAL, "ray grid above 2^31 rays per axis");
+      P.n[k] = (int64_t)nn;
+      P.h[k] = hh;
+      P.x0[k] = P.img_center[k] - 0.5 * (double)(P.n[k] - 1) * hh;
+    }
+    if (P.n[k] < 2 || P.n[k] > 2147483647LL)
+      return fail(MM_EINVAL, "ray grid must have 2 .. 2^31-1 rays per axis");
+  }
+  return MM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pipeline stages
+// ---------------------------------------------------------------------------
+
+static TreeDev tree_dev(const mm_map *h) {
+  TreeDev T;
+  T.keys = h->keys.p;
+  T.sx = h->sx.p;
+  T.sy = h->sy.p;
+  T.sm = h->sm.p;
+  T.n_stars = h->N;
+  T.R0 = h->R0;
+  T.code = h->code.p;
+  T.lvl = h->lvl.p;
+  T.sbeg = h->sbeg.p;
+  T.send = h->send.p;
+  T.first_child = h->first_child.p;
+  T.level_off = h->d_level_off.p;
+  T.depth = h->depth;
+  return T;
+}
+
+template <class F>
+static mm_status cub_call(mm_map *h, bool plan, F &&f) {
+  size_t bytes = 0;
+  CK(f((void *)nullptr, bytes));
+  if (plan) CK(h->cub_tmp.ensure(bytes));
+  if (bytes > h->cub_tmp.n) return fail(MM_ESTATE, "internal: CUB workspace too small");
+  CK(f((void *)h->cub_tmp.p, bytes));
+  return MM_OK;
+}
+
+template <class T>
+static T read_scalar(const T *dptr, cudaStream_t st, cudaError_t &e) {
+  T v{};
+  e = cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return v;
+}
+
+// Morton sort + levels.  plan: learn and store the level counts (host reads).
+static mm_status run_tree(mm_map *h, cudaStream_t st, bool plan) {
+  const int64_t N = h->N;
+  if (plan) {
+    CK(h->keys_in.ensure(N));
+    CK(h->keys.ensure(N));
+    CK(h->idx_in.ensure(N));
+    CK(h->idx.ensure(N));
+    CK(h->sx.ensure(N));
+    CK(h->sy.ensure(N));
+    CK(h->sm.ensure(N));
+  }
+  LCH(launch_star_keys(h->pos_in.p, N, h->R0, h->keys_in.p, h->idx_in.p, st));
+  if (N > 0) {
+    CKS(cub_call(h, plan, [&](void *tmp, size_t &bytes) {
+      return cub::DeviceRadixSort::SortPairs(tmp, bytes, h->keys_in.p, h->keys.p, h->idx_in.p,
+                                             h->idx.p, (int)N, 0, 2 * MM_DMAX, st);
+    }));
+  }
+  LCH(launch_gather_stars(h->pos_in.p, h->m_in.p, h->idx.p, N, h->sx.p, h->sy.p, h->sm.p, st));
+
+  if (plan) {
+    h->level_off.assign(MM_DMAX + 2, 0);
+    h->level_cnt.assign(MM_DMAX + 2, 0);
+    h->level_off[0] = 0;
+    h->level_cnt[0] = 1;
+    h->level_off[1] = 1;
+    CK(h->d_level_off.ensure(MM_DMAX + 2));
+    CK(cudaMemcpyAsync(h->d_level_off.p, h->level_off.data(), (MM_DMAX + 2) * sizeof(int64_t),
+                       cudaMemcpyHostToDevice, st));
+    CK(h->code.ensure(5, true));
+    CK(h->lvl.ensure(5, true));
+    CK(h->sbeg.ensure(5, true));
+    CK(h->send.ensure(5, true));
+    CK(h->first_child.ensure(5, true));
+  }
+  LCH(launch_root_init(N, h->code.p, h->lvl.p, h->sbeg.p, h->send.p, st));
+  for (int l = 0; l <= MM_DMAX; l++) {
+    const int64_t n = h->level_cnt[l];
+    if (plan) {
+      CK(h->split.ensure(n));
+      CK(h->scan.ensure(n));
+    }
+    TreeDev T = tree_dev(h);
+    LCH(launch_level_split(T, l, n, h->leaf_size, h->split.p, st));
+    CKS(cub_call(h, plan, [&](void *tmp, size_t &bytes) {
+      return cub::DeviceScan::ExclusiveSum(tmp, bytes, h->split.p, h->scan.p, (int)n, st);
+    }));
+    if (plan) {
+      cudaError_t e;
+      int32_t a = read_scalar(h->scan.p + (n - 1), st, e);
+      CK(e);
+      int32_t b = read_scalar(h->split.p + (n - 1), st, e);
+      CK(e);
+      const int64_t nxt = 4 * (int64_t)(a + b);
+      h->level_cnt[l + 1] = nxt;
+      h->level_off[l + 1] = h->level_off[l] + n;
+      if (l + 2 <= MM_DMAX + 1) h->level_off[l + 2] = h->level_off[l + 1] + nxt;
+      const int64_t need = h->level_off[l + 1] + nxt;
+      CK(h->code.ensure(need, true));
+      CK(h->lvl.ensure(need, true));
+      CK(h->sbeg.ensure(need, true));
+      CK(h->send.ensure(need, true));
+      CK(h->first_child.ensure(need, true));
+      CK(cudaMemcpyAsync(h->d_level_off.p, h->level_off.data(), (MM_DMAX + 2) * sizeof(int64_t),
+                         cudaMemcpyHostToDevice, st));
+      T = tree_dev(h);
+    }
+    LCH(launch_level_children(T, l, n, h->split.p, h->scan.p, h->code.p, h->lvl.p, h->sbeg.p,
+                             h->send.p, h->first_child.p, st));
+    if (h->level_cnt[l + 1] == 0) {
+      if (plan) {
+        h->depth = l;
+        h->n_nodes = h->level_off[l + 1];
+      }
+      break;
+    }
+  }
+  return MM_OK;
+}
+
+// Active region, expansions, leaf records and the lookup grid.
+static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
+  const mm_params &P = h->P;
+  const int64_t nn = h->n_nodes;
+  TreeDev T = tree_dev(h);
+  if (plan) {
+    CK(h->col_cell.ensure(P.n[0]));
+    CK(h->row_cell.ensure(P.n[1]));
+    CK(h->node_act.ensure(nn));
+    CK(h->leaf_flag.ensure(nn));
+    CK(h->leaf_scan.ensure(nn));
+    CK(h->node_active.ensure(nn));
+  }
+  LCH(launch_axis_cells(P.x0[0], P.h[0], P.n[0], h->R0, h->col_cell.p, st));
+  LCH(launch_axis_cells(P.x0[1], P.h[1], P.n[1], h->R0, h->row_cell.p, st));
+  LCH(launch_active_flags(T, nn, h->col_cell.p, P.n[0], h->row_cell.p, h->row_lo, h->row_hi,
+                         h->node_act.p, h->leaf_flag.p, st));
+  CKS(cub_call(h, plan, [&](void *tmp, size_t &bytes) {
+    return cub::DeviceScan::ExclusiveSum(tmp, bytes, h->leaf_flag.p, h->leaf_scan.p, (int)nn, st);
+  }));
+  if (plan) {
+    cudaError_t e;
+    int32_t a = read_scalar(h->leaf_scan.p + (nn - 1), st, e);
+    CK(e);
+    int32_t b = read_scalar(h->leaf_flag.p + (nn - 1), st, e);
+    CK(e);
+    h->n_active = (int64_t)a + b;
+    if (h->n_active <= 0) return fail(MM_ECUDA, "internal: no active leaf");
+    CK(h->active_list.ensure(h->n_active));
+  }
+  LCH(launch_compact_leaves(nn, h->leaf_flag.p, h->leaf_scan.p, h->node_active.p,
+                           h->active_list.p, st));
+
+  if (plan) {
+    // smallest active leaf and the deepest active level (plan-time analysis)
+    std::vector<int32_t> al(h->n_active), lv(nn);
+    CK(cudaMemcpyAsync(al.data(), h->active_list.p, h->n_active * sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(lv.data(), h->lvl.p, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int ml = 0;
+    for (int32_t id : al) ml = std::max(ml, (int)lv[id]);
+    h->max_leaf_level = ml;
+    h->min_leaf_L = h->R0 / (double)(1ll << ml);
+    // App. C.3: p > log2(<m^2>/<m> / (L |eps|)), eps = 1/10 of the pixel side
+    if (h->p == 0) {
+      double arg = (P.m2_over_m > 0.0) ? P.m2_over_m / (h->min_leaf_L * 0.1 * P.delta) : 1.0;
+      int p = (int)std::floor(std::log2(std::max(arg, 1.0))) + 1;
+      h->p = std::min(MM_PMAX, std::max(2, p));
+    }
+    std::vector<double2> MMh, MLh, LLh;
+    build_operator_tables(h->p, MMh, MLh, LLh);
+    CK(h->MMop.ensure(MMh.size()));
+    CK(h->MLop.ensure(MLh.size()));
+    CK(h->LLop.ensure(LLh.size()));
+    CK(cudaMemcpyAsync(h->MMop.p, MMh.data(), MMh.size() * sizeof(double2),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->MLop.p, MLh.data(), MLh.size() * sizeof(double2),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->LLop.p, LLh.data(), LLh.size() * sizeof(double2),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    CK(h->mp.ensure((size_t)nn * (h->p + 1)));
+    CK(h->loc.ensure((size_t)nn * (h->p + 1)));
+    CK(h->near_cnt.ensure(h->n_active));
+    CK(h->near_off.ensure(h->n_active));
+    CK(h->err.ensure(1));
+  }
+  const int p = h->p, P1 = p + 1;
+  CK(cudaMemsetAsync(h->err.p, 0, sizeof(unsigned), st));
+
+  // up-sweep: P2M at every leaf, then M2M level by level towards the root
+  LCH(launch_p2m(T, nn, p, h->mp.p, st));
+  for (int l = h->depth - 1; l >= 0; l--)
+    LCH(launch_m2m(T, l, h->level_cnt[l], p, h->MMop.p, h->mp.p, st));
+  // down-sweep: levels 0 and 1 have no well-separated nodes
+  CK(cudaMemsetAsync(h->loc.p, 0, (size_t)nn * P1 * sizeof(double2), st));
+  for (int l = 2; l <= h->depth; l++)
+    LCH(launch_local(T, l, h->level_cnt[l], p, h->node_act.p, h->MLop.p, h->LLop.p, h->mp.p,
+                    h->loc.p, h->err.p, st));
+
+  // near-field lists and leaf records
+  LCH(launch_near_count(T, h->n_active, h->active_list.p, h->near_cnt.p, h->err.p, st));
+  CKS(cub_call(h, plan, [&](void *tmp, size_t &bytes) {
+    return cub::DeviceScan::ExclusiveSum(tmp, bytes, h->near_cnt.p, h->near_off.p,
+                                         (int)h->n_active, st);
+  }));
+  if (plan) {
+    cudaError_t e;
+    int32_t a = read_scalar(h->near_off.p + (h->n_active - 1), st, e);
+    CK(e);
+    int32_t b = read_scalar(h->near_cnt.p + (h->n_active - 1), st, e);
+    CK(e);
+    h->n_near = (int64_t)a + b;
+    CK(h->leaf.ensure(h->n_active));
+    CK(h->near_pos.ensure(h->n_near));
+    CK(h->near_m.ensure(h->n_near));
+    CK(h->coef.ensure((size_t)h->n_active * std::max(1, p - 1)));
+  }
+  FmmConst C;
+  C.p = p;
+  C.kappa = P.kappa;
+  C.gamma = P.gamma;
+  C.kappa_star = P.kappa_star;
+  C.x0 = P.x0[0];
+  C.y0 = P.x0[1];
+  C.hx = P.h[0];
+  C.hy = P.h[1];
+  C.lox = P.center_y[0] - P.half_length;
+  C.loy = P.center_y[1] - P.half_length;
+  C.delta = P.delta;
+  LCH(launch_leaf_finalize(T, C, h->n_active, h->active_list.p, h->near_off.p, h->loc.p,
+                          h->leaf.p, h->near_pos.p, h->near_m.p, h->coef.p, h->err.p, st));
+
+  if (plan) {
+    // lookup grid over the active cell rectangle, as deep as 4M entries allow
+    cudaError_t e;
+    int CX0 = read_scalar(h->col_cell.p, st, e);
+    CK(e);
+    int CX1 = read_scalar(h->col_cell.p + (P.n[0] - 1), st, e);
+    CK(e);
+    int CY0 = read_scalar(h->row_cell.p + h->row_lo, st, e);
+    CK(e);
+    int CY1 = read_scalar(h->row_cell.p + h->row_hi, st, e);
+    CK(e);
+    int gl = h->max_leaf_level;
+    for (; gl > 0; gl--) {
+      const int sh = MM_DMAX - gl;
+      const int64_t w = (int64_t)(CX1 >> sh) - (CX0 >> sh) + 1;
+      const int64_t hh = (int64_t)(CY1 >> sh) - (CY0 >> sh) + 1;
+      if (w * hh <= (int64_t)1 << 22) break;
+    }
+    h->glevel = gl;
+    h->gshift = MM_DMAX - gl;
+    h->gx0 = CX0 >> h->gshift;
+    h->gy0 = CY0 >> h->gshift;
+    h->gw = (CX1 >> h->gshift) - h->gx0 + 1;
+    h->gh = (CY1 >> h->gshift) - h->gy0 + 1;
+    CK(h->grid.ensure((size_t)h->gw * h->gh));
+  }
+  LCH(launch_lookup_grid(T, h->node_active.p, h->glevel, h->gx0, h->gy0, h->gw, h->gh,
+                        h->grid.p, st));
+  return MM_OK;
+}
+
+static void fill_mapdev(mm_map *h) {
+  const mm_params &P = h->P;
+  MapDev &M = h->md;
+  memset(&M, 0, sizeof M);
+  M.n0 = P.n[0];
+  M.n1 = P.n[1];
+  M.row_begin = h->row_lo;
+  M.row_end = h->row_hi;
+  M.strips = (int32_t)((P.n[0] - 1 + MM_STRIP - 1) / MM_STRIP);
+  M.rows_per_item = h->rows_per_item;
+  M.row_blocks = (h->row_hi - h->row_lo + h->rows_per_item - 1) / h->rows_per_item;
+  M.work_begin = 0;
+  M.col_cell = h->col_cell.p;
+  M.row_cell = h->row_cell.p;
+  M.grid = h->grid.p;
+  M.glevel = h->glevel;
+  M.gshift = h->gshift;
+  M.gx0 = h->gx0;
+  M.gy0 = h->gy0;
+  M.gw = h->gw;
+  M.gh = h->gh;
+  M.first_child = h->first_child.p;
+  M.node_active = h->node_active.p;
+  M.leaf = h->leaf.p;
+  M.near_pos = h->near_pos.p;
+  M.near_m = h->near_m.p;
+  M.coef = h->coef.p;
+  M.p = h->p;
+  M.square_cells = (P.h[0] == P.h[1]) ? 1 : 0;
+  const double ak = 1.0 - P.kappa + P.kappa_star;
+  M.A1 = (float)((ak + P.gamma) * P.h[0] / P.delta);
+  M.A2 = (float)((ak - P.gamma) * P.h[1] / P.delta);
+  M.sx = (float)(1.0 / (P.h[0] * P.delta));
+  M.sy = (float)(P.h[1] / (P.h[0] * P.h[0] * P.delta));
+  M.rho = (float)((P.h[1] / P.h[0]) * (P.h[1] / P.h[0]));
+  M.npix = P.npix;
+  M.acc = h->acc.p;
+  M.span = h->span.p;
+  M.stat = h->stat.p;
+}
+
+static int shoot_grid() {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  per_sm = MM_SHOOT_MINB;  // resident 256-thread blocks per SM
+  return std::max(1, sms * per_sm);
+}
+
+static mm_status clear_map(mm_map *h, cudaStream_t st) {
+  const size_t np = (size_t)h->P.npix * h->P.npix;
+  CK(cudaMemsetAsync(h->acc.p, 0, np * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(h->span.p, 0, (size_t)h->P.npix * (h->P.npix + 1) * sizeof(unsigned long long),
+                     st));
+  CK(cudaMemsetAsync(h->stat.p, 0, 8 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(h->counter.p, 0, sizeof(unsigned long long), st));
+  return MM_OK;
+}
+
+static double map_scale(const mm_params &P) {
+  return std::ldexp(0.5 * P.h[0] * P.h[1] / (P.delta * P.delta), -32);
+}
+
+static mm_status alloc_map_buffers(mm_map *h) {
+  const size_t np = (size_t)h->P.npix * h->P.npix;
+  CK(h->acc.ensure(np));
+  CK(h->span.ensure((size_t)h->P.npix * (h->P.npix + 1)));
+  CK(h->map.ensure(np));
+  CK(h->stat.ensure(8));
+  CK(h->counter.ensure(1));
+  CK(h->err.ensure(1));
+  CK(h->d_md.ensure(1));
+  return MM_OK;
+}
+
+static mm_status record(mm_map *h, int k, cudaStream_t st) {
+  if (h->opt.time_stages) CK(cudaEventRecord(h->ev[k], st));
+  return MM_OK;
+}
+
+// The FMM pipeline up to (and including) the lookup grid.
+static mm_status prepare(mm_map *h, cudaStream_t st) {
+  CKS(run_tree(h, st, false));
+  CKS(record(h, 1, st));
+  CKS(run_fmm(h, st, false));
+  h->prepared = true;
+  return MM_OK;
+}
+
+static mm_status run_one(mm_map *h, cudaStream_t st) {
+  const mm_params &P = h->P;
+  h->launches = 0;
+  CKS(record(h, 0, st));
+  CKS(clear_map(h, st));
+  if (h->mode == MM_PLAIN_FP64) {
+    CKS(record(h, 1, st));
+    CKS(record(h, 2, st));
+    DirectConst C;
+    C.kappa = P.kappa;
+    C.gamma = P.gamma;
+    C.kappa_star = P.kappa_star;
+    C.x0 = P.x0[0];
+    C.y0 = P.x0[1];
+    C.hx = P.h[0];
+    C.hy = P.h[1];
+    C.lox = P.center_y[0] - P.half_length;
+    C.loy = P.center_y[1] - P.half_length;
+    C.delta = P.delta;
+    LCH(launch_direct64_vertices(h->sx.p, h->sy.p, h->sm.p, h->N, C, P.n[0], h->row_lo,
+                                h->row_hi, h->verts.p, st));
+    LCH(launch_ipm_vertices(h->d_md.p, h->verts.p, P.n[0], h->row_lo, h->row_hi,
+                           h->counter.p, h->err.p, shoot_grid(), st));
+  } else {
+    CKS(prepare(h, st));
+    CKS(record(h, 2, st));
+    const int64_t work = (int64_t)h->md.strips * h->md.row_blocks;
+    LCH(launch_shoot_ipm(h->d_md.p, 1, work, h->md.square_cells != 0, h->counter.p, h->err.p,
+                        shoot_grid(), st));
+  }
+  CKS(record(h, 3, st));
+  LCH(launch_normalize(h->acc.p, h->span.p, P.npix, map_scale(P), h->map.p, st));
+  CKS(record(h, 4, st));
+  h->ev_recorded = h->opt.time_stages != 0;
+  h->last_stream = st;
+  h->ran = true;
+  return MM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *mm_last_error(void) { return g_err.c_str(); }
+
+mm_status mm_derive_params(double kappa_tot, double shear, double smooth_fraction,
+                           int64_t n_stars, const double *masses, double half_length,
+                           int32_t npix, double rays_per_pixel, const mm_options *opt,
+                           mm_params *out) {
+  if (!out) return fail(MM_EINVAL, "out is NULL");
+  mm_options o{};
+  if (opt) o = *opt;
+  return derive(kappa_tot, shear, smooth_fraction, n_stars, masses, half_length, npix,
+                rays_per_pixel, o, *out);
+}
+
+static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double smooth_fraction,
+                             int64_t n_stars, const double *masses, const double *pos_xy,
+                             double half_length, int32_t npix, double rays_per_pixel,
+                             int32_t fmm_order, int32_t leaf_size) {
+  mm_params &P = h->P;
+  CKS(derive(kappa_tot, shear, smooth_fraction, n_stars, masses, half_length, npix,
+             rays_per_pixel, h->opt, P));
+  if (fmm_order < 0 || fmm_order > MM_PMAX)
+    return fail(MM_EINVAL, "fmm_order %d outside [0, %d]", fmm_order, MM_PMAX);
+  if (leaf_size < 0 || leaf_size > 1024)
+    return fail(MM_EINVAL, "leaf_size %d outside [0, 1024]", leaf_size);
+  if (h->opt.mode != MM_FMM_FP32 && h->opt.mode != MM_PLAIN_FP64)
+    return fail(MM_EINVAL, "unknown mode %d", h->opt.mode);
+  if (n_stars > 0 && !pos_xy) return fail(MM_EINVAL, "pos_xy is NULL");
+  if (n_stars > 2000000000LL) return fail(MM_EINVAL, "too many stars");
+  h->mode = h->opt.mode;
+  h->p = fmm_order;
+  h->leaf_size = leaf_size ? leaf_size : 32;
+  h->N = n_stars;
+  h->rows_per_item = h->opt.rows_per_item > 0 ? std::min(h->opt.rows_per_item, 4096) : 64;
+
+  // cell-row band
+  const int64_t rows = P.n[1] - 1;
+  h->row_lo = 0;
+  h->row_hi = rows;
+  if (h->opt.row_begin != 0 || h->opt.row_end != 0) {
+    if (h->opt.row_begin < 0 || h->opt.row_end <= h->opt.row_begin || h->opt.row_end > rows)
+      return fail(MM_EINVAL, "row band [%lld, %lld) outside [0, %lld)",
+                  (long long)h->opt.row_begin, (long long)h->opt.row_end, (long long)rows);
+    h->row_lo = h->opt.row_begin;
+    h->row_hi = h->opt.row_end;
+  }
+
+  // star extent, coverage and root square
+  double ext = 0.0, bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
+  for (int64_t i = 0; i < n_stars; i++) {
+    const double x = pos_xy[2 * i], y = pos_xy[2 * i + 1];
+    if (!std::isfinite(x) || !std::isfinite(y))
+      return fail(MM_EINVAL, "star %lld has a non-finite position", (long long)i);
+    ext = std::max(ext, std::max(std::fabs(x), std::fabs(y)));
+    bx0 = std::min(bx0, x);
+    bx1 = std::max(bx1, x);
+    by0 = std::min(by0, y);
+    by1 = std::max(by1, y);
+  }
+  const double gx0 = P.x0[0], gx1 = P.x0[0] + (double)(P.n[0] - 1) * P.h[0];
+  const double gy0 = P.x0[1], gy1 = P.x0[1] + (double)(P.n[1] - 1) * P.h[1];
+  const bool explicit_region = h->opt.img_half[0] > 0.0 && h->opt.img_half[1] > 0.0;
+  if (P.kappa_star > 0.0 && !explicit_region &&
+      (gx0 < bx0 || gx1 > bx1 || gy0 < by0 || gy1 > by1))
+    return fail(MM_EINVAL,
+                "the stars' bounding box [%g, %g] x [%g, %g] does not cover the shooting "
+                "region [%g, %g] x [%g, %g]",
+                bx0, bx1, by0, by1, gx0, gx1, gy0, gy1);
+  ext = std::max(ext, std::max(std::max(std::fabs(gx0), std::fabs(gx1)),
+                               std::max(std::fabs(gy0), std::fabs(gy1))));
+  h->R0 = std::ldexp(1.0, (int)std::ceil(std::log2(std::max(ext * 1.0001, 1e-3))));
+  if (h->R0 <= ext) h->R0 *= 2.0;
+
+  CK(cudaGetDevice(&h->device));
+  CK(cudaStreamCreateWithFlags(&h->plan_stream, cudaStreamNonBlocking));
+  for (int k = 0; k < 5; k++) CK(cudaEventCreate(&h->ev[k]));
+  cudaStream_t st = h->plan_stream;
+
+  // stars to the device
+  CK(h->pos_in.ensure(2 * n_stars));
+  CK(h->m_in.ensure(n_stars));
+  if (n_stars > 0) {
+    CK(cudaMemcpyAsync(h->pos_in.p, pos_xy, 2 * n_stars * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->m_in.p, masses, n_stars * sizeof(double), cudaMemcpyHostToDevice,
+                       st));
+  }
+  CKS(alloc_map_buffers(h));
+  if (h->mode == MM_PLAIN_FP64) {
+    CK(h->sx.ensure(n_stars));
+    CK(h->sy.ensure(n_stars));
+    CK(h->sm.ensure(n_stars));
+    // unsorted SoA copy
+    CK(h->idx.ensure(n_stars));
+    std::vector<int32_t> id(n_stars);
+    for (int64_t i = 0; i < n_stars; i++) id[i] = (int32_t)i;
+    if (n_stars > 0)
+      CK(cudaMemcpyAsync(h->idx.p, id.data(), n_stars * sizeof(int32_t), cudaMemcpyHostToDevice,
+                         st));
+    LCH(launch_gather_stars(h->pos_in.p, h->m_in.p, h->idx.p, n_stars, h->sx.p, h->sy.p, h->sm.p,
+                           st));
+    CK(h->verts.ensure((size_t)P.n[0] * (h->row_hi - h->row_lo + 1)));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    CKS(run_tree(h, st, true));
+    CKS(run_fmm(h, st, true));
+    CK(cudaStreamSynchronize(st));
+    h->prepared = true;
+  }
+  fill_mapdev(h);
+  CK(cudaMemcpyAsync(h->d_md.p, &h->md, sizeof(MapDev), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  unsigned e = 0;
+  CK(cudaMemcpy(&e, h->err.p, sizeof e, cudaMemcpyDeviceToHost));
+  if (e & ERR_TREE_INVARIANT) return fail(MM_ECUDA, "internal: quadtree invariant violated");
+  h->last_stream = st;
+  return MM_OK;
+}
+
+mm_status mm_create(double kappa_tot, double shear, double smooth_fraction, int64_t n_stars,
+                    const double *masses, const double *pos_xy, double half_length,
+                    int32_t npix, double rays_per_pixel, int32_t fmm_order, int32_t leaf_size,
+                    const mm_options *opt, mm_map **out) {
+  if (!out) return fail(MM_EINVAL, "out is NULL");
+  *out = nullptr;
+  mm_map *h = new (std::nothrow) mm_map();
+  if (!h) return fail(MM_ENOMEM, "host allocation failed");
+  if (opt) h->opt = *opt;
+  mm_status s = create_impl(h, kappa_tot, shear, smooth_fraction, n_stars, masses, pos_xy,
+                            half_length, npix, rays_per_pixel, fmm_order, leaf_size);
+  if (s != MM_OK) {
+    std::string msg = g_err;
+    mm_destroy(h);
+    g_err = msg;
+    return s;
+  }
+  g_err.clear();
+  *out = h;
+  return MM_OK;
+}
+
+mm_status mm_run(mm_map *h, void *stream) {
+  if (!h) return fail(MM_EINVAL, "handle is NULL");
+  if (h->timed_out) return fail(MM_ESTATE, "a previous run timed out");
+  CK(cudaSetDevice(h->device));
+  return run_one(h, (cudaStream_t)stream);
+}
+
+mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
+  if (!hs || n <= 0) return fail(MM_EINVAL, "empty batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < n; i++) {
+    if (!hs[i]) return fail(MM_EINVAL, "handle %d is NULL", i);
+    if (hs[i]->mode != MM_FMM_FP32) return fail(MM_EINVAL, "batch needs MM_FMM_FP32 handles");
+    if (hs[i]->device != hs[0]->device) return fail(MM_EINVAL, "batch spans devices");
+    if (hs[i]->timed_out) return fail(MM_ESTATE, "handle %d timed out earlier", i);
+  }
+  CK(cudaSetDevice(hs[0]->device));
+  mm_map *lead = hs[0];
+  std::vector<MapDev> mds(n);
+  int64_t work = 0;
+  bool all_square = true;
+  for (int i = 0; i < n; i++) {
+    mm_map *h = hs[i];
+    h->launches = 0;
+    CKS(record(h, 0, st));
+    CKS(clear_map(h, st));
+    CKS(prepare(h, st));
+    CKS(record(h, 2, st));
+    mds[i] = h->md;
+    mds[i].work_begin = work;
+    work += (int64_t)h->md.strips * h->md.row_blocks;
+    all_square = all_square && h->md.square_cells;
+  }
+  CK(lead->batch_md.ensure(n));
+  CK(cudaMemcpyAsync(lead->batch_md.p, mds.data(), n * sizeof(MapDev), cudaMemcpyHostToDevice,
+                     st));
+  CK(launch_shoot_ipm(lead->batch_md.p, n, work, all_square, lead->counter.p, lead->err.p,
+                      shoot_grid(), st));
+  lead->launches++;
+  for (int i = 0; i < n; i++) {
+    mm_map *h = hs[i];
+    CKS(record(h, 3, st));
+    LCH(launch_normalize(h->acc.p, h->span.p, h->P.npix, map_scale(h->P), h->map.p, st));
+    CKS(record(h, 4, st));
+    h->ev_recorded = h->opt.time_stages != 0;
+    h->last_stream = st;
+    h->ran = true;
+  }
+  // keep the host copy alive until the copy has been consumed
+  CK(cudaStreamSynchronize(st));
+  return MM_OK;
+}
+
+mm_status mm_get_map(const mm_map *hc, float *out, int32_t on_device) {
+  mm_map *h = const_cast<mm_map *>(hc);
+  if (!h || !out) return fail(MM_EINVAL, "NULL argument");
+  if (!h->ran) return fail(MM_ESTATE, "mm_run has not been called");
+  CK(cudaSetDevice(h->device));
+  const size_t bytes = (size_t)h->P.npix * h->P.npix * sizeof(float);
+  if (on_device) {
+    CK(cudaMemcpyAsync(out, h->map.p, bytes, cudaMemcpyDeviceToDevice, h->last_stream));
+  } else {
+    CK(cudaMemcpyAsync(out, h->map.p, bytes, cudaMemcpyDeviceToHost, h->last_stream));
+    CK(cudaStreamSynchronize(h->last_stream));
+  }
+  return MM_OK;
+}
+
+mm_status mm_get_map_fixed(const mm_map *hc, uint64_t *out, int32_t on_device) {
+  mm_map *h = const_cast<mm_map *>(hc);
+  if (!h || !out) return fail(MM_EINVAL, "NULL argument");
+  if (!h->ran) return fail(MM_ESTATE, "mm_run has not been called");
+  CK(cudaSetDevice(h->device));
+  const size_t np = (size_t)h->P.npix * h->P.npix;
+  CK(h->fixed_out.ensure(np));
+  LCH(launch_fold_span(h->acc.p, h->span.p, h->P.npix, h->fixed_out.p, h->last_stream));
+  if (on_device) {
+    CK(cudaMemcpyAsync(out, h->fixed_out.p, np * 8, cudaMemcpyDeviceToDevice, h->last_stream));
+  } else {
+    CK(cudaMemcpyAsync(out, h->fixed_out.p, np * 8, cudaMemcpyDeviceToHost, h->last_stream));
+    CK(cudaStreamSynchronize(h->last_stream));
+  }
+  return MM_OK;
+}
+
+mm_status mm_shoot_points(mm_map *h, int64_t n, const double *z_xy, double *w_xy) {
+  if (!h) return fail(MM_EINVAL, "handle is NULL");
+  if (n < 0 || (n > 0 && (!z_xy || !w_xy))) return fail(MM_EINVAL, "bad point arrays");
+  if (n == 0) return MM_OK;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = h->plan_stream;
+  CK(cudaStreamSynchronize(h->last_stream));
+  double *dz = nullptr, *dw = nullptr;
+  CK(cudaMalloc(&dz, 2 * n * sizeof(double)));
+  cudaError_t e = cudaMalloc(&dw, 2 * n * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(dz);
+    CK(e);
+  }
+  mm_status s = MM_OK;
+  do {
+    const mm_params &P = h->P;
+    if (cudaMemcpyAsync(dz, z_xy, 2 * n * sizeof(double), cudaMemcpyHostToDevice, st)) {
+      s = fail(MM_ECUDA, "copy of probe points failed");
+      break;
+    }
+    if (h->mode == MM_PLAIN_FP64) {
+      DirectConst C;
+      C.kappa = P.kappa;
+      C.gamma = P.gamma;
+      C.kappa_star = P.kappa_star;
+      C.x0 = P.x0[0];
+      C.y0 = P.x0[1];
+      C.hx = P.h[0];
+      C.hy = P.h[1];
+      C.lox = P.center_y[0] - P.half_length;
+      C.loy = P.center_y[1] - P.half_length;
+      C.delta = P.delta;
+      e = launch_direct64_points(h->sx.p, h->sy.p, h->sm.p, h->N, C, n, dz, dw, st);
+    } else {
+      if (!h->prepared) {
+        s = prepare(h, st);
+        if (s != MM_OK) break;
+      }
+      e = launch_probe(h->d_md.p, h->md.square_cells != 0, n, dz, dw, P.x0[0], P.x0[1], P.h[0],
+                       P.h[1], h->R0, P.center_y[0] - P.half_length,
+                       P.center_y[1] - P.half_length, P.delta, h->err.p, st);
+    }
+    if (e != cudaSuccess) {
+      s = fail(MM_ECUDA, "probe launch: %s", cudaGetErrorString(e));
+      break;
+    }
+    e = cudaMemcpyAsync(w_xy, dw, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = fail(MM_ECUDA, "probe: %s", cudaGetErrorString(e));
+  } while (0);
+  cudaFree(dz);
+  cudaFree(dw);
+  return s;
+}
+
+mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
+  mm_map *h = const_cast<mm_map *>(hc);
+  if (!h || !out) return fail(MM_EINVAL, "NULL argument");
+  CK(cudaSetDevice(h->device));
+  memset(out, 0, sizeof *out);
+  out->params = h->P;
+  out->mode = h->mode;
+  out->fmm_order = h->mode == MM_FMM_FP32 ? h->p : 0;
+  out->leaf_size = h->leaf_size;
+  out->depth = h->depth;
+  out->n_stars = h->N;
+  out->nodes = h->n_nodes;
+  out->active_leaves = h->n_active;
+  out->root_half_length = h->R0;
+  out->min_leaf_half_length = h->min_leaf_L;
+  out->rays = h->P.n[0] * (h->row_hi - h->row_lo + 1);
+  out->cells = (h->P.n[0] - 1) * (h->row_hi - h->row_lo);
+  out->ms_tree = out->ms_expansions = out->ms_shoot = out->ms_normalize = out->ms_total = -1.0;
+  if (h->last_stream || h->ran) CK(cudaStreamSynchronize(h->last_stream));
+  if (h->mode == MM_FMM_FP32 && h->n_nodes > 0) {
+    std::vector<int32_t> fc(h->n_nodes);
+    CK(cudaMemcpy(fc.data(), h->first_child.p, h->n_nodes * sizeof(int32_t),
+                  cudaMemcpyDeviceToHost));
+    int64_t leaves = 0;
+    for (int32_t c : fc) leaves += (c < 0);
+    out->leaves = leaves;
+    // vertex-weighted mean near-field size over active leaves
+    std::vector<LeafRec> lr(h->n_active);
+    CK(cudaMemcpy(lr.data(), h->leaf.p, h->n_active * sizeof(LeafRec), cudaMemcpyDeviceToHost));
+    double sw = 0.0, swn = 0.0;
+    const double L = 1.0;
+    (void)L;
+    std::vector<int32_t> lv(h->n_nodes);
+    CK(cudaMemcpy(lv.data(), h->lvl.p, h->n_nodes * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (const LeafRec &r : lr) {
+      const double side = 2.0 * h->R0 / (double)(1ll << lv[r.node]);
+      const double w = side * side;  // vertices per leaf scale with its area
+      sw += w;
+      swn += w * r.near_cnt;
+    }
+    out->mean_near_stars = sw > 0 ? swn / sw : 0.0;
+  }
+  if (h->ran) {
+    unsigned long long st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    CK(cudaMemcpy(st, h->stat.p, sizeof st, cudaMemcpyDeviceToHost));
+    out->triangles_dropped = (int64_t)st[0];
+    out->triangles_clipped = (int64_t)st[1];
+    out->triangles_quad = (int64_t)st[2];
+    out->triangles_strip = (int64_t)st[3];
+    out->triangles_span = (int64_t)st[4];
+  }
+  out->kernel_launches = h->launches;
+  if (h->ev_recorded) {
+    float a = 0, b = 0, c = 0, d = 0;
+    CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[4]));
+    out->ms_total = a;
+    if (h->mode == MM_FMM_FP32) {
+      CK(cudaEventElapsedTime(&b, h->ev[0], h->ev[1]));
+      CK(cudaEventElapsedTime(&c, h->ev[1], h->ev[2]));
+      out->ms_tree = b;
+      out->ms_expansions = c;
+    }
+    CK(cudaEventElapsedTime(&d, h->ev[2], h->ev[3]));
+    out->ms_shoot = d;
+    CK(cudaEventElapsedTime(&a, h->ev[3], h->ev[4]));
+    out->ms_normalize = a;
+  }
+  return MM_OK;
+}
+
+void mm_destroy(mm_map *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->last_stream) cudaStreamSynchronize(h->last_stream);
+  DBuf<double> *dbs[] = {&h->pos_in, &h->m_in, &h->sx, &h->sy, &h->sm};
+  for (auto *b : dbs) b->release();
+  h->keys_in.release();
+  h->keys.release();
+  h->idx_in.release();
+  h->idx.release();
+  h->cub_tmp.release();
+  h->d_level_off.release();
+  h->code.release();
+  DBuf<int32_t> *ibs[] = {&h->lvl,       &h->sbeg,      &h->send,      &h->first_child,
+                          &h->split,     &h->scan,      &h->col_cell,  &h->row_cell,
+                          &h->node_act,  &h->leaf_flag, &h->leaf_scan, &h->node_active,
+                          &h->active_list, &h->near_cnt, &h->near_off, &h->grid};
+  for (auto *b : ibs) b->release();
+  DBuf<double2> *cbs[] = {&h->MMop, &h->MLop, &h->LLop, &h->mp, &h->loc};
+  for (auto *b : cbs) b->release();
+  h->leaf.release();
+  h->near_pos.release();
+  h->near_m.release();
+  h->coef.release();
+  h->acc.release();
+  h->span.release();
+  h->stat.release();
+  h->counter.release();
+  h->fixed_out.release();
+  h->err.release();
+  h->map.release();
+  h->d_md.release();
+  h->verts.release();
+  h->batch_md.release();
+  for (auto &e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->plan_stream) cudaStreamDestroy(h->plan_stream);
+  delete h;
+}
+
+}  // extern "C"

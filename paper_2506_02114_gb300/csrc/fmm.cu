@@ -1,0 +1,444 @@
+// Multipole and local expansions of the quadtree FMM (App. C.2), FP64.
+//
+// Coefficients are complex and normalised to the node half-length L about
+// the node centre, as in App. C.2:
+//   multipole  psi(z) = a_0 log(zeta) + sum_{k=1..p} a_k zeta^-k
+//   local      psi(z) = sum_{l=0..p} c_l zeta^l,      zeta = (z - z_node)/L.
+// The three shift operators depend only on the relative position of the two
+// nodes in units of L, so they are fixed (p+1)x(p+1) complex matrices built
+// once on the host: 4 for M2M (child quadrant), 49 slots (40 used) for M2L
+// (same-level offsets in [-3, 3]^2 with Chebyshev distance >= 2) and 4 for
+// L2L.  Each is stored as [op][k][l] so that threads indexed by the output
+// coefficient l read consecutive entries.
+//
+// The l = 0 (logarithmic) terms of the locals are not formed: the deflection
+// needs only dpsi/dz (Sec. 3.3), so c_0 never reaches a ray.
+#include <cmath>
+#include <vector>
+
+#include "mm_kernels.h"
+
+namespace mm {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// z^k by repeated squaring (k >= 0)
+__device__ __forceinline__ double2 cpow(double2 z, int k) {
+  double2 r = make_double2(1.0, 0.0);
+  while (k > 0) {
+    if (k & 1) r = cmul(r, z);
+    z = cmul(z, z);
+    k >>= 1;
+  }
+  return r;
+}
+
+__device__ __forceinline__ void node_geom(const TreeDev &T, int64_t node, int &level, int &cx,
+                                          int &cy, double &zx, double &zy, double &L) {
+  level = T.lvl[node];
+  uint32_t x, y;
+  morton_decode(T.code[node], x, y);
+  cx = (int)x;
+  cy = (int)y;
+  const double side = 2.0 * T.R0 / (double)(1ll << level);
+  zx = -T.R0 + ((double)cx + 0.5) * side;
+  zy = -T.R0 + ((double)cy + 0.5) * side;
+  L = 0.5 * side;
+}
+
+// Node id of the level-`level` cell (x, y), or -1 if that cell is not a node.
+__device__ __forceinline__ int64_t find_node(const TreeDev &T, int level, int x, int y) {
+  const int side = 1 << level;
+  if (x < 0 || y < 0 || x >= side || y >= side) return -1;
+  const uint64_t c = morton2((uint32_t)x, (uint32_t)y);
+  int64_t lo = T.level_off[level], hi = T.level_off[level + 1];
+  int64_t k = lower_bound_u64(T.code, lo, hi, c);
+  return (k < hi && T.code[k] == c) ? k : -1;
+}
+
+// ---------------------------------------------------------------------------
+// P2M: a_0 = sum m_i, a_k = -(1/k) sum m_i zeta_i^k  (leaves only)
+// ---------------------------------------------------------------------------
+__global__ void k_p2m(TreeDev T, int64_t n_nodes, int p, double2 *mp) {
+  const int64_t node = blockIdx.x;
+  if (node >= n_nodes || T.first_child[node] >= 0) return;
+  const int k = threadIdx.x;
+  if (k > p) return;
+  int level, cx, cy;
+  double zx, zy, L;
+  node_geom(T, node, level, cx, cy, zx, zy, L);
+  const double invL = 1.0 / L;
+  double2 s = make_double2(0.0, 0.0);
+  for (int64_t i = T.sbeg[node]; i < T.send[node]; i++) {
+    const double m = T.sm[i];
+    if (k == 0) {
+      s.x += m;
+    } else {
+      double2 zeta = make_double2((T.sx[i] - zx) * invL, (T.sy[i] - zy) * invL);
+      double2 zk = cpow(zeta, k);
+      s.x = fma(m, zk.x, s.x);
+      s.y = fma(m, zk.y, s.y);
+    }
+  }
+  if (k > 0) s = make_double2(-s.x / k, -s.y / k);
+  mp[node * (p + 1) + k] = s;
+}
+
+// ---------------------------------------------------------------------------
+// M2M: parent b = sum over the four children of MM[q] a_child (App. C.2)
+// ---------------------------------------------------------------------------
+__global__ void k_m2m(TreeDev T, int level, int64_t n, int p, const double2 *__restrict__ MMop,
+                      double2 *mp) {
+  const int64_t node = T.level_off[level] + blockIdx.x;
+  if ((int64_t)blockIdx.x >= n) return;
+  const int fc = T.first_child[node];
+  if (fc < 0) return;
+  __shared__ double2 a[4][MM_PMAX + 1];
+  const int P1 = p + 1;
+  for (int idx = threadIdx.x; idx < 4 * P1; idx += blockDim.x)
+    a[idx / P1][idx % P1] = mp[(int64_t)(fc + idx / P1) * P1 + idx % P1];
+  __syncthreads();
+  const int l = threadIdx.x;
+  if (l > p) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int q = 0; q < 4; q++) {
+    const double2 *op = MMop + (int64_t)q * P1 * P1;
+    for (int k = 0; k <= l; k++) s = cfma(op[k * P1 + l], a[q][k], s);
+  }
+  mp[node * P1 + l] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Locals of an active node at level >= 2 (App. C.2):
+//   L2L from the parent, M2L from the parent's neighbours' children that are
+//   not adjacent (<= 27), P2L from the parent's unsplit neighbours that are
+//   not adjacent (<= 5).
+// ---------------------------------------------------------------------------
+__global__ void k_local(TreeDev T, int level, int64_t n, int p, const int32_t *node_act,
+                        const double2 *__restrict__ MLop, const double2 *__restrict__ LLop,
+                        const double2 *__restrict__ mp, double2 *loc, unsigned *err) {
+  if ((int64_t)blockIdx.x >= n) return;
+  const int64_t node = T.level_off[level] + blockIdx.x;
+  if (!node_act[node]) return;
+  __shared__ double2 src[MM_PMAX + 1];
+  const int P1 = p + 1;
+  const int l = threadIdx.x;
+  const bool on = l <= p && l >= 1;
+  int lv, nx, ny;
+  double zx, zy, L;
+  node_geom(T, node, lv, nx, ny, zx, zy, L);
+  const int px = nx >> 1, py = ny >> 1;
+  double2 acc = make_double2(0.0, 0.0);
+
+  // L2L from the parent
+  const int64_t parent = find_node(T, level - 1, px, py);
+  if (parent >= 0) {
+    for (int k = threadIdx.x; k < P1; k += blockDim.x) src[k] = loc[parent * P1 + k];
+    __syncthreads();
+    const int q = (nx & 1) | ((ny & 1) << 1);
+    const double2 *op = LLop + (int64_t)q * P1 * P1;
+    if (on)
+      for (int k = l; k <= p; k++) acc = cfma(op[k * P1 + l], src[k], acc);
+    __syncthreads();
+  }
+
+  const double invL = 1.0 / L;
+  for (int dy = -1; dy <= 1; dy++)
+    for (int dx = -1; dx <= 1; dx++) {
+      if (dx == 0 && dy == 0) continue;
+      const int qx = px + dx, qy = py + dy;
+      const int side = 1 << (level - 1);
+      if (qx < 0 || qy < 0 || qx >= side || qy >= side) continue;
+      const int64_t qid = find_node(T, level - 1, qx, qy);
+      if (qid < 0) {
+        if (threadIdx.x == 0) atomicOr(err, ERR_TREE_INVARIANT);
+        continue;
+      }
+      const int fc = T.first_child[qid];
+      if (fc >= 0) {
+        for (int c = 0; c < 4; c++) {
+          const int ox = 2 * qx + (c & 1) - nx, oy = 2 * qy + (c >> 1) - ny;
+          if (abs(ox) <= 1 && abs(oy) <= 1) continue;  // neighbour: near field
+          for (int k = threadIdx.x; k < P1; k += blockDim.x)
+            src[k] = mp[(int64_t)(fc + c) * P1 + k];
+          __syncthreads();
+          const double2 *op = MLop + (int64_t)((oy + 3) * 7 + (ox + 3)) * P1 * P1;
+          if (on)
+            for (int k = 0; k <= p; k++) acc = cfma(op[k * P1 + l], src[k], acc);
+          __syncthreads();
+        }
+      } else {
+        // unsplit parent-neighbour: adjacent to the node unless its 2x2
+        // level cells all lie at Chebyshev distance >= 2
+        const int x0 = 2 * qx, y0 = 2 * qy;
+        const bool adj = (x0 + 1 >= nx - 1 && x0 <= nx + 1) && (y0 + 1 >= ny - 1 && y0 <= ny + 1);
+        if (adj) continue;
+        if (on) {
+          for (int64_t i = T.sbeg[qid]; i < T.send[qid]; i++) {
+            double2 zeta = make_double2((T.sx[i] - zx) * invL, (T.sy[i] - zy) * invL);
+            const double d = zeta.x * zeta.x + zeta.y * zeta.y;
+            double2 inv = make_double2(zeta.x / d, -zeta.y / d);
+            double2 zl = cpow(inv, l);
+            const double f = -T.sm[i] / (double)l;
+            acc.x = fma(f, zl.x, acc.x);
+            acc.y = fma(f, zl.y, acc.y);
+          }
+        }
+      }
+    }
+  if (l <= p) loc[node * P1 + l] = on ? acc : make_double2(0.0, 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Near field of an active leaf: the leaf, its same-level neighbour cells that
+// are nodes (with all their descendants), and the unsplit nodes one level up
+// covering the missing neighbour cells.
+// ---------------------------------------------------------------------------
+template <class F>
+__device__ __forceinline__ int for_each_near_range(const TreeDev &T, int64_t node, F &&f,
+                                                   unsigned *err) {
+  int level, nx, ny;
+  double zx, zy, L;
+  node_geom(T, node, level, nx, ny, zx, zy, L);
+  if (level == 0) {
+    f(T.sbeg[node], T.send[node]);
+    return 0;
+  }
+  int64_t seen[9];
+  int nseen = 0;
+  for (int dy = -1; dy <= 1; dy++)
+    for (int dx = -1; dx <= 1; dx++) {
+      const int x = nx + dx, y = ny + dy;
+      const int side = 1 << level;
+      if (x < 0 || y < 0 || x >= side || y >= side) continue;
+      int64_t id = find_node(T, level, x, y);
+      if (id >= 0) {
+        f(T.sbeg[id], T.send[id]);
+        continue;
+      }
+      int64_t pid = find_node(T, level - 1, x >> 1, y >> 1);
+      if (pid < 0) {
+        atomicOr(err, ERR_TREE_INVARIANT);
+        continue;
+      }
+      bool dup = false;
+      for (int s = 0; s < nseen; s++) dup |= (seen[s] == pid);
+      if (dup) continue;
+      seen[nseen++] = pid;
+      f(T.sbeg[pid], T.send[pid]);
+    }
+  return 0;
+}
+
+__global__ void k_near_count(TreeDev T, int64_t n_active, const int32_t *active_list,
+                             int32_t *near_cnt, unsigned *err) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_active) return;
+  int64_t total = 0;
+  for_each_near_range(T, active_list[t], [&](int64_t b, int64_t e) { total += e - b; }, err);
+  near_cnt[t] = (int32_t)total;
+}
+
+__global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_active,
+                                const int32_t *active_list, const int32_t *near_off,
+                                const double2 *__restrict__ loc, LeafRec *leaf,
+                                NearPos *near_pos, float *near_m, float2 *coef,
+                                unsigned *err) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_active) return;
+  const int64_t node = active_list[t];
+  int level, nx, ny;
+  double zx, zy, L;
+  node_geom(T, node, level, nx, ny, zx, zy, L);
+  const int p = C.p, P1 = p + 1;
+
+  // reference grid vertex nearest the centre
+  const double gi = rint((zx - C.x0) / C.hx), gj = rint((zy - C.y0) / C.hy);
+  const double xr = C.x0 + gi * C.hx, yr = C.y0 + gj * C.hy;
+  LeafRec R;
+  R.i_ref = (int32_t)gi;
+  R.j_ref = (int32_t)gj;
+  R.fcx = (float)((zx - xr) / C.hx);
+  R.fcy = (float)((zy - yr) / C.hy);
+
+  // FP64 image of the centre: macro model + sheet - far field at the centre
+  const double2 c1 = (p >= 1) ? loc[node * P1 + 1] : make_double2(0.0, 0.0);
+  const double ak = 1.0 - C.kappa + C.kappa_star;
+  const double Wx = (ak + C.gamma) * zx - c1.x / L;
+  const double Wy = (ak - C.gamma) * zy + c1.y / L;  // - conj(c1/L)
+  double U = (Wx - C.lox) / C.delta, V = (Wy - C.loy) / C.delta;
+  U = fmin(fmax(U, -1.0e9), 1.0e9);
+  V = fmin(fmax(V, -1.0e9), 1.0e9);
+  const double Ui = floor(U), Vi = floor(V);
+  R.Ui = (int32_t)Ui;
+  R.Vi = (int32_t)Vi;
+  R.Uf = (float)(U - Ui);
+  R.Vf = (float)(V - Vi);
+  R.zsx = (float)(C.hx / L);
+  R.zsy = (float)(C.hy / L);
+  R.near_off = near_off[t];
+  R.coef_off = (int32_t)(t * (p > 1 ? p - 1 : 1));
+  R.node = (int32_t)node;
+  R.pad0 = R.pad1 = 0;
+
+  // near-field stars in the leaf's grid frame
+  int64_t k = R.near_off;
+  for_each_near_range(
+      T, node,
+      [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; i++) {
+          const double sxg = (T.sx[i] - xr) / C.hx, syg = (T.sy[i] - yr) / C.hy;
+          const double Kx = rint(sxg), Ky = rint(syg);
+          NearPos np;
+          np.Kx = (float)Kx;
+          np.fx = (float)(sxg - Kx);
+          np.Ky = (float)Ky;
+          np.fy = (float)(syg - Ky);
+          near_pos[k] = np;
+          near_m[k] = (float)T.sm[i];
+          k++;
+        }
+      },
+      err);
+  R.near_cnt = (int32_t)(k - R.near_off);
+  leaf[t] = R;
+
+  // far-field coefficients e_l = l c_l / (L delta), l = 2..p
+  const double s = 1.0 / (L * C.delta);
+  for (int l = 2; l <= p; l++) {
+    const double2 c = loc[node * P1 + l];
+    coef[R.coef_off + (l - 2)] = make_float2((float)(l * c.x * s), (float)(l * c.y * s));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host: operator tables and launchers
+// ---------------------------------------------------------------------------
+
+struct cplx {
+  double x, y;
+};
+static inline cplx cm(cplx a, cplx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+static inline cplx cpw(cplx z, int k) {
+  cplx r{1.0, 0.0};
+  for (int i = 0; i < k; i++) r = cm(r, z);
+  return r;
+}
+static inline cplx cinv(cplx z) {
+  double d = z.x * z.x + z.y * z.y;
+  return {z.x / d, -z.y / d};
+}
+
+// binomial coefficients C(n, k) for n <= 2 p (Pascal's triangle, FP64)
+static std::vector<std::vector<double>> binomials(int nmax) {
+  std::vector<std::vector<double>> C(nmax + 1, std::vector<double>(nmax + 1, 0.0));
+  for (int n = 0; n <= nmax; n++) {
+    C[n][0] = 1.0;
+    for (int k = 1; k <= n; k++) C[n][k] = C[n - 1][k - 1] + (k <= n - 1 ? C[n - 1][k] : 0.0);
+  }
+  return C;
+}
+
+void build_operator_tables(int p, std::vector<double2> &MM, std::vector<double2> &ML,
+                           std::vector<double2> &LL) {
+  const int P1 = p + 1;
+  auto C = binomials(2 * p + 1);
+  MM.assign((size_t)4 * P1 * P1, make_double2(0.0, 0.0));
+  LL.assign((size_t)4 * P1 * P1, make_double2(0.0, 0.0));
+  ML.assign((size_t)49 * P1 * P1, make_double2(0.0, 0.0));
+  for (int q = 0; q < 4; q++) {
+    // M2M: child centre relative to the parent, in child half-lengths
+    cplx z0{(q & 1) ? 1.0 : -1.0, (q >> 1) ? 1.0 : -1.0};
+    double2 *op = &MM[(size_t)q * P1 * P1];
+    op[0 * P1 + 0] = make_double2(1.0, 0.0);
+    for (int l = 1; l <= p; l++) {
+      const double s = std::ldexp(1.0, -l);
+      cplx zl = cpw(z0, l);
+      op[0 * P1 + l] = make_double2(-zl.x / l * s, -zl.y / l * s);
+      for (int k = 1; k <= l; k++) {
+        cplx zz = cpw(z0, l - k);
+        double b = C[l - 1][k - 1] * s;
+        op[k * P1 + l] = make_double2(zz.x * b, zz.y * b);
+      }
+    }
+    // L2L: child centre relative to the parent, in parent half-lengths
+    cplx w0{(q & 1) ? 0.5 : -0.5, (q >> 1) ? 0.5 : -0.5};
+    double2 *ol = &LL[(size_t)q * P1 * P1];
+    for (int l = 0; l <= p; l++) {
+      const double s = std::ldexp(1.0, -l);
+      for (int k = l; k <= p; k++) {
+        cplx zz = cpw(w0, k - l);
+        double b = C[k][l] * s;
+        ol[k * P1 + l] = make_double2(zz.x * b, zz.y * b);
+      }
+    }
+  }
+  // M2L: source centre relative to the target, z0 = 2 (dx + i dy)
+  for (int dy = -3; dy <= 3; dy++)
+    for (int dx = -3; dx <= 3; dx++) {
+      if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
+      cplx z0{2.0 * dx, 2.0 * dy};
+      cplx iz = cinv(z0);
+      cplx imz = cinv(cplx{-z0.x, -z0.y});
+      double2 *op = &ML[(size_t)((dy + 3) * 7 + (dx + 3)) * P1 * P1];
+      for (int l = 1; l <= p; l++) {
+        cplx izl = cpw(iz, l);
+        op[0 * P1 + l] = make_double2(-izl.x / l, -izl.y / l);
+        for (int k = 1; k <= p; k++) {
+          cplx t = cm(izl, cpw(imz, k));
+          double b = C[l + k - 1][k - 1];
+          op[k * P1 + l] = make_double2(t.x * b, t.y * b);
+        }
+      }
+    }
+}
+
+static inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+static inline int coef_threads(int p) { return 32 * ((p + 1 + 31) / 32); }
+
+cudaError_t launch_p2m(const TreeDev &T, int64_t n_nodes, int p, double2 *mp, cudaStream_t st) {
+  if (n_nodes <= 0) return cudaSuccess;
+  k_p2m<<<(unsigned)n_nodes, coef_threads(p), 0, st>>>(T, n_nodes, p, mp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_m2m(const TreeDev &T, int level, int64_t n, int p, const double2 *MMop,
+                       double2 *mp, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_m2m<<<(unsigned)n, coef_threads(p), 0, st>>>(T, level, n, p, MMop, mp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local(const TreeDev &T, int level, int64_t n, int p, const int32_t *node_act,
+                         const double2 *MLop, const double2 *LLop, const double2 *mp,
+                         double2 *loc, unsigned *err, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_local<<<(unsigned)n, coef_threads(p), 0, st>>>(T, level, n, p, node_act, MLop, LLop, mp,
+                                                   loc, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_count(const TreeDev &T, int64_t n_active, const int32_t *active_list,
+                              int32_t *near_cnt, unsigned *err, cudaStream_t st) {
+  if (n_active <= 0) return cudaSuccess;
+  k_near_count<<<blocks_for(n_active, 128), 128, 0, st>>>(T, n_active, active_list, near_cnt,
+                                                         err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_finalize(const TreeDev &T, const FmmConst &C, int64_t n_active,
+                                 const int32_t *active_list, const int32_t *near_off,
+                                 const double2 *loc, LeafRec *leaf, NearPos *near_pos,
+                                 float *near_m, float2 *coef, unsigned *err, cudaStream_t st) {
+  if (n_active <= 0) return cudaSuccess;
+  k_leaf_finalize<<<blocks_for(n_active, 64), 64, 0, st>>>(T, C, n_active, active_list, near_off,
+                                                           loc, leaf, near_pos, near_m, coef,
+                                                           err);
+  return cudaGetLastError();
+}
+
+}  // namespace mm

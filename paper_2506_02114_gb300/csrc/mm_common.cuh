@@ -1,0 +1,122 @@
+// Shared device-side types and helpers of the libmm CUDA path (sm_103a).
+//
+// Coordinates: theta_star = 1.  The quadtree root is the square
+// [-R0, R0)^2 with R0 a power of two, so every cell edge at every level is an
+// exact binary fraction.  Cell indices at the finest level MM_DMAX are 21-bit
+// integers; a level-l cell index is the finest index shifted right by
+// (MM_DMAX - l).  Morton codes interleave x (even bits) and y (odd bits).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define MM_DMAX 21            // deepest quadtree level
+#define MM_PMAX 64            // largest expansion order accepted by the ABI
+#define MM_STRIP 31           // cell columns per warp work item (32 vertex columns)
+#define MM_BIG_PIXELS 32      // bbox area (in pixels, inside the map) above which a
+                              // triangle is apportioned by the whole warp, row by row
+
+namespace mm {
+
+// Error word bits written by kernels (read back by the host).
+enum : unsigned int {
+  ERR_TREE_INVARIANT = 1u,    // a split node lacks a same-level neighbour
+  ERR_LOOKUP = 2u,            // a ray vertex fell outside every active leaf
+};
+
+// Per active leaf: everything a ray vertex in the leaf needs (64 bytes).
+// Positions inside the leaf are measured in ray-grid units from the grid
+// vertex (i_ref, j_ref) closest to the leaf centre; the leaf centre sits at
+// (i_ref + fcx, j_ref + fcy) in those units.
+struct __align__(16) LeafRec {
+  int32_t i_ref, j_ref;
+  float fcx, fcy;
+  int32_t Ui, Vi;             // integer part of the centre's image in pixels
+  float Uf, Vf;               // fractional part (FP64-accurate)
+  float zsx, zsy;             // h_x / L, h_y / L : grid units -> zeta units
+  int32_t near_off, near_cnt; // near-field stars in MapDev::near_pos/near_m
+  int32_t coef_off;           // first of (p - 1) far-field coefficients
+  int32_t node;               // tree node id
+  int32_t pad0, pad1;
+};
+
+// Near-field star in the leaf's grid frame: grid position relative to
+// (i_ref, j_ref) = (Kx + fx, Ky + fy), K integer-valued, |f| <= 0.5.
+struct __align__(16) NearPos {
+  float Kx, fx, Ky, fy;
+};
+
+// A mapped ray vertex in canonical pixel form: integer pixel plus the
+// position inside it; px == INT_MIN marks a non-finite vertex.
+struct __align__(16) Vtx {
+  int px, py;
+  float fx, fy;
+};
+
+// Everything the deflection + mapping kernel needs about one map.
+struct MapDev {
+  // ray grid
+  int64_t n0, n1;             // vertices per axis
+  int64_t row_begin, row_end; // cell rows [row_begin, row_end)
+  int32_t strips, rows_per_item;
+  int64_t row_blocks;
+  int64_t work_begin;         // first global work item of this map
+  // leaf lookup
+  const int32_t *col_cell, *row_cell;   // finest-level cell index per vertex column / row
+  const int32_t *grid;                  // lookup grid: active leaf id, or -(node+1)
+  int32_t glevel, gshift, gx0, gy0, gw, gh;
+  const int32_t *first_child;           // per node: first child id, -1 for a leaf
+  const int32_t *node_active;           // per node: active leaf id or -1
+  // leaves
+  const LeafRec *leaf;
+  const NearPos *near_pos;
+  const float *near_m;
+  const float2 *coef;
+  int32_t p;                  // expansion order
+  int32_t square_cells;       // 1 when h_x == h_y
+  // per-ray constants (pixel units)
+  float A1, A2;               // (1 - kappa + kappa_star +- gamma) h / delta
+  float sx, sy;               // 1/(h_x delta), h_y/(h_x^2 delta)
+  float rho;                  // (h_y/h_x)^2
+  // map
+  int32_t npix;
+  unsigned long long *acc;    // npix*npix fixed point, 2^32 = one triangle
+  unsigned long long *span;   // npix*(npix+1) row difference array
+  // statistics (per map)
+  unsigned long long *stat;   // triangle counters, see IpmCounters
+};
+
+// Interleave two 21-bit integers: x in even bits, y in odd bits.
+__host__ __device__ __forceinline__ uint64_t morton2(uint32_t x, uint32_t y) {
+  uint64_t r = 0;
+#pragma unroll
+  for (int b = 0; b < MM_DMAX; b++) {
+    r |= (uint64_t)((x >> b) & 1u) << (2 * b);
+    r |= (uint64_t)((y >> b) & 1u) << (2 * b + 1);
+  }
+  return r;
+}
+
+__host__ __device__ __forceinline__ void morton_decode(uint64_t c, uint32_t &x, uint32_t &y) {
+  x = 0;
+  y = 0;
+#pragma unroll
+  for (int b = 0; b < MM_DMAX; b++) {
+    x |= (uint32_t)((c >> (2 * b)) & 1u) << b;
+    y |= (uint32_t)((c >> (2 * b + 1)) & 1u) << b;
+  }
+}
+
+// First index in [lo, hi) with a[idx] >= key (a sorted ascending).
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *a, int64_t lo, int64_t hi,
+                                                   uint64_t key) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace mm

@@ -1,0 +1,350 @@
+// Fused ray deflection + inverse polygon mapping (the hot kernel), the
+// normalisation kernel and the deflection probe.
+//
+// Per ray vertex (Sec. 3.3, App. C): the vertex's leaf supplies
+//   - the near-field stars (the leaf and its neighbours, at most leaf_size):
+//     direct sum of m / conj(z - z_i);
+//   - the local (Taylor) expansion of the far field about the leaf centre:
+//     alpha_far = conj(dpsi/dz), dpsi/dz = (1/L) sum_l l c_l zeta^(l-1);
+//   - the FP64 image of the leaf centre W_c (macro model + sheet + far field
+//     at the centre), so that only small, centre-relative quantities are
+//     evaluated in FP32 per ray.
+// The lens equation (Sec. 2.2, circular sheet of Sec. 3.1) then gives
+//   w - W_c = (1-kappa+kappa_*) d + gamma conj(d) - alpha_near
+//             - conj(sum_{l>=2} l c_l zeta^(l-1) / L),   d = z - z_c.
+#include "ipm.cuh"
+#include "mm_kernels.h"
+
+namespace mm {
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Active leaf containing finest-level cell (cx, cy); -1 if none.
+__device__ __forceinline__ int lookup_leaf(const MapDev &M, int cx, int cy) {
+  int gx = (cx >> M.gshift) - M.gx0, gy = (cy >> M.gshift) - M.gy0;
+  if (gx < 0 || gy < 0 || gx >= M.gw || gy >= M.gh) return -1;
+  int e = __ldg(&M.grid[(int64_t)gy * M.gw + gx]);
+  if (e >= 0) return e;
+  int node = -e - 1;
+  for (int lvl = M.glevel + 1; lvl <= MM_DMAX; lvl++) {
+    int fc = __ldg(&M.first_child[node]);
+    if (fc < 0) break;
+    int sh = MM_DMAX - lvl;
+    node = fc + (((cx >> sh) & 1) | (((cy >> sh) & 1) << 1));
+  }
+  return __ldg(&M.node_active[node]);
+}
+
+// Source-plane position of grid point (i + ti, j + tj) in pixel units:
+// returns the integer pixel and the fraction.  ti = tj = 0 for ray vertices.
+template <bool SQUARE, bool FRAC>
+__device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i, int64_t j,
+                                           float ti, float tj, bool valid) {
+  const int4 *rp = reinterpret_cast<const int4 *>(M.leaf + (leaf < 0 ? 0 : leaf));
+  int4 q0 = __ldg(rp), q1 = __ldg(rp + 1), q2 = __ldg(rp + 2), q3 = __ldg(rp + 3);
+  const int i_ref = q0.x, j_ref = q0.y;
+  const float fcx = __int_as_float(q0.z), fcy = __int_as_float(q0.w);
+  const int Ui = q1.x, Vi = q1.y;
+  const float Uf = __int_as_float(q1.z), Vf = __int_as_float(q1.w);
+  const float zsx = __int_as_float(q2.x), zsy = __int_as_float(q2.y);
+  const int near_off = q2.z, near_cnt = (leaf < 0) ? 0 : q2.w;
+  const int coef_off = q3.x;
+
+  // vertex position relative to the reference vertex, in grid units (exact
+  // integers), and relative to the leaf centre
+  const float fi = (float)(int)(i - i_ref), fj = (float)(int)(j - j_ref);
+  float gx = fi - fcx, gy = fj - fcy;
+  if (FRAC) {
+    gx += ti;
+    gy += tj;
+  }
+
+  // near field: S = sum m g / |g|^2 in grid units (|g|^2 = gx^2 + rho gy^2)
+  float Sx = 0.f, Sy = 0.f;
+  const int maxcnt = __reduce_max_sync(0xffffffffu, near_cnt);
+  for (int k = 0; k < maxcnt; k++) {
+    if (k < near_cnt) {
+      const float4 s = __ldg(reinterpret_cast<const float4 *>(M.near_pos) + near_off + k);
+      const float m = __ldg(M.near_m + near_off + k);
+      float dx = (fi - s.x) - s.y;  // (i - i_ref - Kx) - fx: exact near the star
+      float dy = (fj - s.z) - s.w;
+      if (FRAC) {
+        dx += ti;
+        dy += tj;
+      }
+      float r2 = SQUARE ? fmaf(dx, dx, dy * dy) : fmaf(dx, dx, M.rho * dy * dy);
+      float qq = m * rcp_approx(r2);
+      Sx = fmaf(qq, dx, Sx);
+      Sy = fmaf(qq, dy, Sy);
+    }
+  }
+
+  // far field: f = sum_{l=2}^{p} e_l zeta^(l-1), e_l = l c_l / (L delta)
+  float fr = 0.f, fim = 0.f;
+  const int p = M.p;
+  if (p >= 2 && leaf >= 0) {
+    const float zx = gx * zsx, zy = gy * zsy;
+    const float2 *e = M.coef + coef_off;
+    float2 t = __ldg(e + (p - 2));
+    fr = t.x;
+    fim = t.y;
+    for (int l = p - 3; l >= 0; l--) {
+      float2 c = __ldg(e + l);
+      float nr = fmaf(fr, zx, fmaf(-fim, zy, c.x));
+      float ni = fmaf(fr, zy, fmaf(fim, zx, c.y));
+      fr = nr;
+      fim = ni;
+    }
+    float nr = fr * zx - fim * zy;
+    float ni = fr * zy + fim * zx;
+    fr = nr;
+    fim = ni;
+  }
+
+  float u = Uf + (fmaf(M.A1, gx, -Sx * M.sx) - fr);
+  float v = Vf + (fmaf(M.A2, gy, -Sy * M.sy) + fim);
+  Vtx out;
+  if (!valid || leaf < 0 || !isfinite(u) || !isfinite(v)) {
+    out.px = MM_VTX_INVALID;
+    out.py = MM_VTX_INVALID;
+    out.fx = 0.f;
+    out.fy = 0.f;
+    return out;
+  }
+  const float lim = 536870912.0f;  // 2^29 pixels: far outside any map
+  u = fminf(fmaxf(u, -lim), lim);
+  v = fminf(fmaxf(v, -lim), lim);
+  float flu = floorf(u), flv = floorf(v);
+  out.px = Ui + (int)flu;
+  out.py = Vi + (int)flv;
+  out.fx = u - flu;
+  out.fy = v - flv;
+  return out;
+}
+
+__device__ __forceinline__ Vtx shfl_down_vtx(const Vtx &v, int d) {
+  Vtx r;
+  r.px = __shfl_down_sync(0xffffffffu, v.px, d);
+  r.py = __shfl_down_sync(0xffffffffu, v.py, d);
+  r.fx = __shfl_down_sync(0xffffffffu, v.fx, d);
+  r.fy = __shfl_down_sync(0xffffffffu, v.fy, d);
+  return r;
+}
+
+// Warp-reduce the per-lane triangle counters into the map's statistics.
+__device__ __forceinline__ void flush_counters(const MapDev &M, IpmCounters &cnt, int lane) {
+  unsigned long long v[5] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big};
+#pragma unroll
+  for (int k = 0; k < 5; k++) {
+    for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);
+    if (lane == 0 && v[k]) atomicAdd(&M.stat[k], v[k]);
+  }
+  cnt = IpmCounters{0, 0, 0, 0, 0};
+}
+
+// Persistent warps; each work item is a strip of 31 cell columns by
+// rows_per_item cell rows of one map.  Lane l computes vertex column
+// 31*s + l for every vertex row of the item, keeps the previous row in
+// registers and takes its right neighbour's vertices by shuffle; lanes 0..30
+// then map cells (i, j-1) as the triangles {v00, v10, v11} and
+// {v00, v11, v01} (diagonal from lower-left to upper-right).
+#ifndef MM_SHOOT_MINB
+#define MM_SHOOT_MINB 2  // resident 256-thread blocks per SM the register budget targets
+#endif
+
+template <bool SQUARE>
+__global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *__restrict__ maps, int n_maps,
+                                                   int64_t total_work,
+                                                   unsigned long long *work_counter,
+                                                   unsigned *err) {
+  const int lane = threadIdx.x & 31;
+  __shared__ SmallTri s_queue[8][64];
+  WarpQueue wq = {s_queue[threadIdx.x >> 5], 0};
+  IpmCounters cnt = {0, 0, 0, 0, 0};
+  int last_map = -1;
+  while (true) {
+    unsigned long long w = 0;
+    if (lane == 0) w = atomicAdd(work_counter, 1ull);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if ((int64_t)w >= total_work) break;
+    int mi = 0;
+    if (n_maps > 1) {
+      int lo = 0, hi = n_maps - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (maps[mid].work_begin <= (int64_t)w)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      mi = lo;
+    }
+    const MapDev &M = maps[mi];
+    if (mi != last_map) {  // warp-uniform
+      if (last_map >= 0) flush_counters(maps[last_map], cnt, lane);
+      last_map = mi;
+    }
+    const int64_t local = (int64_t)w - M.work_begin;
+    const int64_t s = local % M.strips, b = local / M.strips;
+    const int64_t i = s * MM_STRIP + lane;
+    const int64_t jb = M.row_begin + b * M.rows_per_item;
+    int64_t je = jb + M.rows_per_item;
+    if (je > M.row_end) je = M.row_end;
+    const bool vvalid = i < M.n0;
+    const int cx = __ldg(&M.col_cell[vvalid ? i : M.n0 - 1]);
+    const bool cell_col = (lane < MM_STRIP) && (i + 1 < M.n0);
+    RunAcc ra = {LLONG_MIN, LLONG_MIN, 0ull};
+    Vtx prev;
+    {
+      const int leaf = lookup_leaf(M, cx, __ldg(&M.row_cell[jb]));
+      if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
+      prev = shoot_point<SQUARE, false>(M, leaf, i, jb, 0.f, 0.f, vvalid);
+    }
+    for (int64_t j = jb + 1; j <= je; j++) {
+      const int cy = __ldg(&M.row_cell[j]);
+      const int leaf = lookup_leaf(M, cx, cy);
+      if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
+      Vtx cur = shoot_point<SQUARE, false>(M, leaf, i, j, 0.f, 0.f, vvalid);
+      Vtx cur_r = shfl_down_vtx(cur, 1);
+      Vtx prev_r = shfl_down_vtx(prev, 1);
+#pragma unroll 1
+      for (int tri = 0; tri < 2; tri++) {
+        TriJob job;
+        SmallTri se;
+        const int code = cell_col ? ipm_triangle(M, prev, tri ? cur_r : prev_r,
+                                                 tri ? cur : cur_r, ra, cnt, se, job)
+                                  : TRI_DONE;
+        wq_push(M, wq, code == TRI_SMALL, se, lane);
+        warp_row_jobs(M, code == TRI_ROWS, job, lane);
+      }
+      prev = cur;
+    }
+    run_flush(M, ra);
+    wq_drain(M, wq, lane);
+  }
+  if (last_map >= 0) flush_counters(maps[last_map], cnt, lane);
+}
+
+// mu = (acc + row-prefix(span)) * 2^-32 * (h_x h_y / 2) / delta^2; one block
+// per map row.
+__global__ void __launch_bounds__(256) k_normalize(const unsigned long long *__restrict__ acc,
+                                                   const unsigned long long *__restrict__ span,
+                                                   int npix, double scale, float *out) {
+  __shared__ unsigned long long part[256];
+  const int row = blockIdx.x;
+  const int t = threadIdx.x;
+  const int chunk = (npix + 255) / 256;
+  const int c0 = t * chunk, c1 = min(npix, c0 + chunk);
+  const unsigned long long *sp = span + (int64_t)row * (npix + 1);
+  unsigned long long s = 0;
+  for (int c = c0; c < c1; c++) s += sp[c];
+  part[t] = s;
+  __syncthreads();
+  // inclusive scan of the 256 partial sums (Hillis-Steele)
+  for (int d = 1; d < 256; d <<= 1) {
+    unsigned long long v = (t >= d) ? part[t - d] : 0ull;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  unsigned long long run = (t > 0) ? part[t - 1] : 0ull;
+  const unsigned long long *ar = acc + (int64_t)row * npix;
+  float *o = out + (int64_t)row * npix;
+  for (int c = c0; c < c1; c++) {
+    run += sp[c];
+    unsigned long long tot = ar[c] + run;
+    o[c] = (float)((double)tot * scale);
+  }
+}
+
+// acc += row-prefix(span): folds the difference array into the accumulator so
+// the raw fixed-point map can be read back.
+__global__ void k_fold_span(unsigned long long *acc, const unsigned long long *span, int npix,
+                            unsigned long long *out) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= npix) return;
+  const unsigned long long *sp = span + (int64_t)row * (npix + 1);
+  unsigned long long run = 0;
+  for (int c = 0; c < npix; c++) {
+    run += sp[c];
+    out[(int64_t)row * npix + c] = acc[(int64_t)row * npix + c] + run;
+  }
+}
+
+// Deflection probe: w (FP64) at arbitrary image-plane points, through the
+// same per-vertex code as the map kernel.
+template <bool SQUARE>
+__global__ void k_probe(const MapDev *maps, int64_t n, const double *z, double *w, double x0,
+                        double y0, double hx, double hy, double R0, double lox, double loy,
+                        double delta, unsigned *err) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = t < n;
+  const MapDev &M = maps[0];
+  double zx = ok ? z[2 * t] : x0, zy = ok ? z[2 * t + 1] : y0;
+  double gi = (zx - x0) / hx, gj = (zy - y0) / hy;
+  double fi = floor(gi), fj = floor(gj);
+  int64_t i = (int64_t)fi, j = (int64_t)fj;
+  float ti = (float)(gi - fi), tj = (float)(gj - fj);
+  const double scale = (double)(1 << MM_DMAX) / (2.0 * R0);
+  double cxd = floor((zx + R0) * scale), cyd = floor((zy + R0) * scale);
+  int cx = (int)fmin(fmax(cxd, 0.0), (double)((1 << MM_DMAX) - 1));
+  int cy = (int)fmin(fmax(cyd, 0.0), (double)((1 << MM_DMAX) - 1));
+  int leaf = ok ? lookup_leaf(M, cx, cy) : -1;
+  Vtx v = shoot_point<SQUARE, true>(M, leaf, i, j, ti, tj, ok && leaf >= 0);
+  if (!ok) return;
+  if (v.px == MM_VTX_INVALID) {
+    w[2 * t] = nan("");
+    w[2 * t + 1] = nan("");
+    return;
+  }
+  w[2 * t] = lox + ((double)v.px + (double)v.fx) * delta;
+  w[2 * t + 1] = loy + ((double)v.py + (double)v.fy) * delta;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_shoot_ipm(const MapDev *d_maps, int n_maps, int64_t total_work,
+                             bool square, unsigned long long *counter, unsigned *err, int grid,
+                             cudaStream_t st) {
+  if (total_work <= 0) return cudaSuccess;
+  if (square)
+    k_shoot_ipm<true><<<grid, 256, 0, st>>>(d_maps, n_maps, total_work, counter, err);
+  else
+    k_shoot_ipm<false><<<grid, 256, 0, st>>>(d_maps, n_maps, total_work, counter, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(const unsigned long long *acc, const unsigned long long *span,
+                             int npix, double scale, float *out, cudaStream_t st) {
+  k_normalize<<<npix, 256, 0, st>>>(acc, span, npix, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_span(unsigned long long *acc, const unsigned long long *span, int npix,
+                             unsigned long long *out, cudaStream_t st) {
+  k_fold_span<<<(npix + 127) / 128, 128, 0, st>>>(acc, span, npix, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe(const MapDev *d_maps, bool square, int64_t n, const double *z,
+                         double *w, double x0, double y0, double hx, double hy, double R0,
+                         double lox, double loy, double delta, unsigned *err,
+                         cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (square)
+    k_probe<true><<<(unsigned)blocks, 256, 0, st>>>(d_maps, n, z, w, x0, y0, hx, hy, R0, lox,
+                                                    loy, delta, err);
+  else
+    k_probe<false><<<(unsigned)blocks, 256, 0, st>>>(d_maps, n, z, w, x0, y0, hx, hy, R0, lox,
+                                                     loy, delta, err);
+  return cudaGetLastError();
+}
+
+}  // namespace mm

@@ -1,0 +1,95 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+symbol include/mm.h declares; host-side parameter derivation agrees with the
+oracle's independent derivation; invalid arguments are rejected; and with no
+GPU the product path fails loudly instead of falling back."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2506_02114_gb300 as mm
+import synthetic
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = mm.lib()
+    names = declared_functions()
+    assert set(names) == set(mm.EXPORTS)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("case", [
+    dict(kappa=0.5, gamma=0.4, s=0.5, npix=2000, hl=10.0, rpp=9.0),
+    dict(kappa=0.8, gamma=0.25, s=0.0, npix=500, hl=10.0, rpp=2.25),
+    dict(kappa=0.3, gamma=0.45, s=0.2, npix=50, hl=2.5, rpp=4.0, center_y=(1.5, -0.75)),
+    dict(kappa=1.3, gamma=0.2, s=0.9, npix=64, hl=3.0, rpp=1.0),
+    dict(kappa=0.4, gamma=0.3, s=0.0, npix=256, hl=4.0, img_half=(16 / 3, 16.0),
+         ray_grid=(700, 2000)),
+])
+def test_derived_parameters_match_oracle(oracle_mod, case):
+    m, _ = synthetic.star_field(9, 300, 10.0, synthetic.SALPETER_01_1)
+    kw = {}
+    for k in ("center_y", "img_half", "ray_grid"):
+        if k in case:
+            kw[k] = case[k]
+    got = mm.derive_params(case["kappa"], case["gamma"], case["s"], m, case["hl"], case["npix"],
+                           case.get("rpp", 0.0), **kw).as_dict()
+    ref = oracle_mod.derive_params(case["kappa"], case["gamma"], case["s"], m, case["hl"],
+                                   case["npix"], rays_per_pixel=case.get("rpp", 0.0),
+                                   **kw).as_dict()
+    for k in ("kappa_star", "a1", "a2", "mu_macro", "mean_m", "m2_over_m", "r_border",
+              "delta", "img_center", "img_half", "h", "x0"):
+        np.testing.assert_allclose(got[k], ref[k], rtol=1e-14, atol=1e-14, err_msg=k)
+    assert list(got["n"]) == list(ref["n"])
+
+
+def test_invalid_arguments_rejected():
+    with pytest.raises(mm.MMError) as e:
+        mm.derive_params(0.5, 0.5, 0.0, [1.0], 1.0, 8, 1.0)
+    assert e.value.status == mm.MM_EINVAL and "critical" in str(e.value)
+    for bad in [dict(s=1.5), dict(hl=0.0), dict(npix=0)]:
+        args = dict(kappa=0.5, gamma=0.2, s=0.0, hl=1.0, npix=8)
+        args.update(bad)
+        with pytest.raises(mm.MMError) as e:
+            mm.derive_params(args["kappa"], args["gamma"], args["s"], [1.0], args["hl"],
+                             args["npix"], 1.0)
+        assert e.value.status == mm.MM_EINVAL
+    with pytest.raises(mm.MMError):
+        mm.derive_params(0.5, 0.2, 0.0, [1.0, -1.0], 1.0, 8, 1.0)
+    with pytest.raises(mm.MMError):   # kappa_star > 0 needs stars
+        mm.derive_params(0.5, 0.2, 0.0, [], 1.0, 8, 1.0)
+
+
+def test_create_rejects_bad_orders_before_touching_a_gpu():
+    m, pos = synthetic.star_field(1, 50, 10.0)
+    for fo, ls in [(-1, 0), (65, 0), (10, -2), (10, 2000)]:
+        with pytest.raises(mm.MMError) as e:
+            mm.create(0.3, 0.1, 0.0, m, pos, 1.0, 16, 1.0, fmm_order=fo, leaf_size=ls)
+        assert e.value.status == mm.MM_EINVAL
+
+
+def test_create_rejects_uncovered_region():
+    m, pos = synthetic.star_field(1, 50, 2.0)   # far too small a disk
+    with pytest.raises(mm.MMError) as e:
+        mm.create(0.4, 0.1, 0.0, m, pos, 5.0, 16, 1.0)
+    assert e.value.status == mm.MM_EINVAL and "cover" in str(e.value)
+
+
+def test_no_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m, pos = synthetic.star_field(1, 60, 12.0)
+    with pytest.raises(mm.MMError) as e:
+        mm.create(0.3, 0.1, 0.0, m, pos, 1.0, 16, img_half=(2.0, 2.0), ray_grid=(8, 8))
+    assert e.value.status in (mm.MM_ECUDA, mm.MM_ENOMEM)
