@@ -204,6 +204,43 @@ mm_status mm_shoot_points(mm_map *h, int64_t n, const double *z_xy, double *w_xy
  * (synchronises the handle's last stream). */
 mm_status mm_get_stats(const mm_map *h, mm_stats *out);
 
+/*
+ * Plain FP64 map into caller-provided buffers, allocating nothing.  The paper
+ * has no counterpart: this serves callers that cannot call cudaMalloc --
+ * those that have handed all device memory to their own pool allocator (a
+ * library allocation would fail or escape their accounting) and those that
+ * cannot accept the device-wide synchronisation a cudaMalloc may imply.
+ *
+ * Computes the same map as mm_create(mode = MM_PLAIN_FP64, explicit ray
+ * grid) + mm_run + mm_get_map(on_device = 1): direct FP64 sum over every star
+ * for each ray vertex, then inverse polygon mapping, on `stream`
+ * (asynchronous; synchronise before reading map_out).
+ *
+ *   kappa_tot, shear, smooth_fraction: as in mm_create.
+ *   masses[n_stars], pos_xy[2*n_stars]: DEVICE pointers, interleaved (x, y).
+ *   half_length, npix, center_y[2] (host, may be NULL = origin): the map.
+ *   ray_grid[2] (host): rays per axis; grid_origin[2], grid_spacing[2]
+ *     (host): image-plane position of vertex (0, 0) and the ray spacings,
+ *     e.g. mm_params.n, .x0 and .h of an equivalent handle.
+ *   map_out: DEVICE pointer, npix*npix floats, row-major, row = y.
+ *
+ * Scratch lives in one fixed device array inside the library (about 9.5 MB,
+ * held by every GPU that loads it until the process exits), so sizes are
+ * bounded: n_stars <= 16384, npix <= 256, ray_grid[0]*ray_grid[1] <= 2^19;
+ * larger requests return MM_EINVAL with a message and do nothing.  The first
+ * call on each device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  All calls share
+ * the array and each call clears what it accumulates, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race and
+ * corrupt each other's maps: serialise them.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ */
+mm_status mm_map_plain_fp64_noalloc(double kappa_tot, double shear, double smooth_fraction,
+                                    int64_t n_stars, const double *masses, const double *pos_xy,
+                                    double half_length, int32_t npix, const double *center_y,
+                                    const int64_t *ray_grid, const double *grid_origin,
+                                    const double *grid_spacing, float *map_out, void *stream);
+
 /* Thread-local message describing the last failed call ("" if none). */
 const char *mm_last_error(void);
 

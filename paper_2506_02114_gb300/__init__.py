@@ -81,8 +81,8 @@ class Stats(ctypes.Structure):
 
 
 EXPORTS = ["mm_derive_params", "mm_create", "mm_run", "mm_run_batch", "mm_get_map",
-           "mm_get_map_fixed", "mm_shoot_points", "mm_get_stats", "mm_last_error",
-           "mm_destroy"]
+           "mm_get_map_fixed", "mm_shoot_points", "mm_get_stats", "mm_map_plain_fp64_noalloc",
+           "mm_last_error", "mm_destroy"]
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -124,6 +124,10 @@ def lib(build_if_missing=True):
     L.mm_shoot_points.argtypes = [_vp, ctypes.c_int64, _dp, _dp]
     L.mm_get_stats.restype = ctypes.c_int
     L.mm_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
+    L.mm_map_plain_fp64_noalloc.restype = ctypes.c_int
+    L.mm_map_plain_fp64_noalloc.argtypes = [
+        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64, _vp, _vp,
+        ctypes.c_double, ctypes.c_int32, _dp, ctypes.POINTER(ctypes.c_int64), _dp, _dp, _vp, _vp]
     L.mm_last_error.restype = ctypes.c_char_p
     L.mm_last_error.argtypes = []
     L.mm_destroy.restype = None
@@ -255,6 +259,25 @@ def shoot_points(h: Handle, z_xy):
     w = np.empty_like(z)
     _check(lib().mm_shoot_points(h.ptr, z.shape[0], _ptr(z), w.ctypes.data_as(_dp)))
     return w
+
+
+def map_plain_fp64_noalloc(kappa, gamma, s, masses_dev, pos_dev, half_length, npix, ray_grid,
+                           grid_origin, grid_spacing, map_out_dev, center_y=(0.0, 0.0),
+                           stream=None):
+    """Plain FP64 map with no device allocation (see mm.h): masses_dev,
+    pos_dev ((n, 2) or (2n,)) and map_out_dev (npix*npix float32) are CUDA
+    tensors; the grid arguments are host sequences.  Asynchronous."""
+    n = int(masses_dev.numel())
+    rg = (ctypes.c_int64 * 2)(int(ray_grid[0]), int(ray_grid[1]))
+    org = (ctypes.c_double * 2)(float(grid_origin[0]), float(grid_origin[1]))
+    hh = (ctypes.c_double * 2)(float(grid_spacing[0]), float(grid_spacing[1]))
+    cy = (ctypes.c_double * 2)(float(center_y[0]), float(center_y[1]))
+    _check(lib().mm_map_plain_fp64_noalloc(
+        float(kappa), float(gamma), float(s), n, _vp(masses_dev.data_ptr() if n else 0),
+        _vp(pos_dev.data_ptr() if n else 0), float(half_length), int(npix),
+        ctypes.cast(cy, _dp), rg, ctypes.cast(org, _dp), ctypes.cast(hh, _dp),
+        _vp(map_out_dev.data_ptr()), _vp(current_stream() if stream is None else stream)))
+    return map_out_dev
 
 
 def get_stats(h: Handle) -> dict:

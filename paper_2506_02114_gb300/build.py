@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmm.so")
 
-SOURCES = ["api.cu", "tree.cu", "fmm.cu", "shoot.cu", "direct64.cu"]
+SOURCES = ["api.cu", "tree.cu", "fmm.cu", "shoot.cu", "direct64.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -45,6 +45,11 @@ static mm_status fail(mm_status s, const char *fmt, ...) {
   return s;
 }
 
+namespace mm {
+// Lets other translation units of the library report through mm_last_error.
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace mm
+
 #define CK(call)                                                                        \
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \

@@ -10,6 +10,9 @@
 
 namespace mm {
 
+// Message returned by mm_last_error on this thread (api.cu).
+void set_last_error(const char *msg);
+
 // ---- tree (tree.cu) --------------------------------------------------------
 struct TreeDev {
   // sorted stars (Morton order), SoA, FP64
