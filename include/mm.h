@@ -70,6 +70,8 @@ typedef struct {
   int64_t row_end;          /*   ray grid; both 0 -> every row */
   int32_t rows_per_item;    /* rows of cells per warp work item, 1..4096; 0 -> 64 */
   int32_t reserved;
+  int64_t col_begin;        /* shoot only cell columns [col_begin, col_end) of */
+  int64_t col_end;          /*   the ray grid; both 0 -> every column */
 } mm_options;
 
 /* Every derived scalar of a run (host-side numbers; no GPU needed). */
@@ -111,9 +113,9 @@ typedef struct {
   int64_t cells;            /* grid cells mapped by mm_run */
   int64_t triangles_dropped;/* zero-area or non-finite triangles (last run) */
   int64_t triangles_clipped;/* triangles spanning more than one pixel of the map */
-  int64_t triangles_quad;   /*   of which within a 2 x 2 pixel box (closed form) */
-  int64_t triangles_strip;  /*   of which clipped by column/row strips */
-  int64_t triangles_span;   /*   of which walked row by row by a whole warp */
+  int64_t triangles_quad;   /*   of which within a 2 x 2 pixel box */
+  int64_t triangles_box;    /*   of which with a box of at most 64 map pixels */
+  int64_t triangles_rows;   /*   of which larger (pixel rows shared by a warp) */
   int64_t kernel_launches;  /* library kernels launched by the last run (CUB's
                                sort/scan kernels and memsets not counted) */
   /* stage times of the last mm_run in ms (time_stages = 1), else -1 */

@@ -73,6 +73,10 @@ def lib():
         L.or_map.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _dp, _dp,
                              ctypes.c_int64, ctypes.c_int64, _dp, _dp,
                              ctypes.POINTER(MapStats), ctypes.c_int]
+        L.or_map_tile.restype = ctypes.c_int
+        L.or_map_tile.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _dp, _dp,
+                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                  _dp, _dp, ctypes.POINTER(MapStats), ctypes.c_int]
         L.or_map_from_vertices.restype = ctypes.c_int
         L.or_map_from_vertices.argtypes = [ctypes.POINTER(Params), _dp, ctypes.c_int64,
                                            ctypes.c_int64, _dp, _dp,
@@ -150,6 +154,25 @@ def magnification_map(params: Params, masses, pos_xy, row_begin=0, row_end=0,
         raise ValueError("oracle: bad row range or out of memory")
     stats = {"triangles": st.triangles, "dropped": st.dropped, "pieces": st.pieces}
     return (mu, acc, stats) if return_acc else (mu, stats)
+
+
+def magnification_map_tile(params: Params, masses, pos_xy, row_begin, row_end, col_begin,
+                           col_end, nthreads=None):
+    """Map from the cells of rows [row_begin, row_end) and columns
+    [col_begin, col_end) of the ray grid."""
+    m = _f64(masses)
+    xy = _f64(pos_xy).reshape(-1, 2)
+    n = params.npix
+    mu = np.zeros((n, n), dtype=np.float64)
+    acc = np.zeros((n, n), dtype=np.float64)
+    st = MapStats()
+    rc = lib().or_map_tile(ctypes.byref(params), m.size, _ptr(m), _ptr(xy), int(row_begin),
+                           int(row_end), int(col_begin), int(col_end), mu.ctypes.data_as(_dp),
+                           acc.ctypes.data_as(_dp), ctypes.byref(st),
+                           nthreads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle: bad tile or out of memory")
+    return mu, {"triangles": st.triangles, "dropped": st.dropped, "pieces": st.pieces}
 
 
 def map_from_vertices(params: Params, w_xy, row_begin, row_end, nthreads=None):

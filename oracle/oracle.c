@@ -121,6 +121,7 @@ typedef struct {
   int64_t begin, end;
   const double *z_xy; /* explicit points, or NULL for grid vertices */
   int64_t row0;       /* first vertex row when z_xy == NULL */
+  int64_t col0, width;/* vertex columns [col0, col0 + width) when z_xy == NULL */
   double *w_xy;
 } deflect_job;
 
@@ -133,8 +134,8 @@ static void *deflect_worker(void *arg) {
       x = J->z_xy[2 * k];
       y = J->z_xy[2 * k + 1];
     } else {
-      int64_t i = k % p->n[0];
-      int64_t j = J->row0 + k / p->n[0];
+      int64_t i = J->col0 + k % J->width;
+      int64_t j = J->row0 + k / J->width;
       x = p->x0[0] + (double)i * p->h[0];
       y = p->x0[1] + (double)j * p->h[1];
     }
@@ -146,8 +147,8 @@ static void *deflect_worker(void *arg) {
 
 static void run_deflect(const or_params *p, int64_t n_stars,
                         const double *masses, const double *pos_xy, int64_t n,
-                        const double *z_xy, int64_t row0, double *w_xy,
-                        int nthreads) {
+                        const double *z_xy, int64_t row0, int64_t col0,
+                        int64_t width, double *w_xy, int nthreads) {
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 256) nthreads = 256;
   pthread_t th[256];
@@ -161,6 +162,8 @@ static void run_deflect(const or_params *p, int64_t n_stars,
     jobs[t].end = n * (t + 1) / nthreads;
     jobs[t].z_xy = z_xy;
     jobs[t].row0 = row0;
+    jobs[t].col0 = col0;
+    jobs[t].width = width;
     jobs[t].w_xy = w_xy;
   }
   if (nthreads == 1) {
@@ -174,7 +177,7 @@ static void run_deflect(const or_params *p, int64_t n_stars,
 void or_deflect(const or_params *p, int64_t n_stars, const double *masses,
                 const double *pos_xy, int64_t n, const double *z_xy,
                 double *w_xy, int nthreads) {
-  run_deflect(p, n_stars, masses, pos_xy, n, z_xy, 0, w_xy, nthreads);
+  run_deflect(p, n_stars, masses, pos_xy, n, z_xy, 0, 0, 1, w_xy, nthreads);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -242,8 +245,9 @@ double or_tri_rect_area(const double *tri, double xlo, double ylo, double xhi,
 
 typedef struct {
   const or_params *p;
-  const double *w_xy; /* vertices of rows [vrow0, ...], n[0] per row */
+  const double *w_xy; /* vertices of rows [vrow0, ...], columns [col0, col1] */
   int64_t vrow0;
+  int64_t col0, col1; /* cell columns [col0, col1) */
   int64_t crow_begin, crow_end; /* cell rows handled by this worker */
   double *acc;                  /* npix*npix partial sums */
   or_map_stats st;
@@ -289,14 +293,14 @@ static void apportion_triangle(const double *tri, int npix, double *acc,
 static void *map_worker(void *arg) {
   map_job *J = (map_job *)arg;
   const or_params *p = J->p;
-  int64_t n0 = p->n[0];
+  int64_t width = J->col1 - J->col0 + 1; /* vertices per stored row */
   double inv = 1.0 / p->delta;
   double lo0 = p->center_y[0] - p->half_length;
   double lo1 = p->center_y[1] - p->half_length;
   for (int64_t j = J->crow_begin; j < J->crow_end; j++) {
-    const double *r0 = J->w_xy + 2 * (j - J->vrow0) * n0;
-    const double *r1 = r0 + 2 * n0;
-    for (int64_t i = 0; i + 1 < n0; i++) {
+    const double *r0 = J->w_xy + 2 * (j - J->vrow0) * width - 2 * J->col0;
+    const double *r1 = r0 + 2 * width;
+    for (int64_t i = J->col0; i < J->col1; i++) {
       /* vertices of cell (i, j) in pixel units */
       double v00[2] = {(r0[2 * i] - lo0) * inv, (r0[2 * i + 1] - lo1) * inv};
       double v10[2] = {(r0[2 * i + 2] - lo0) * inv, (r0[2 * i + 3] - lo1) * inv};
@@ -312,11 +316,12 @@ static void *map_worker(void *arg) {
   return NULL;
 }
 
-int or_map_from_vertices(const or_params *p, const double *w_xy,
-                         int64_t row_begin, int64_t row_end,
-                         double *mu_out, double *acc_out, or_map_stats *stats,
-                         int nthreads) {
+static int map_tile_from_vertices(const or_params *p, const double *w_xy,
+                                  int64_t row_begin, int64_t row_end, int64_t col_begin,
+                                  int64_t col_end, double *mu_out, double *acc_out,
+                                  or_map_stats *stats, int nthreads) {
   if (row_begin < 0 || row_end <= row_begin || row_end > p->n[1] - 1) return -1;
+  if (col_begin < 0 || col_end <= col_begin || col_end > p->n[0] - 1) return -1;
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 256) nthreads = 256;
   int64_t rows = row_end - row_begin;
@@ -330,6 +335,8 @@ int or_map_from_vertices(const or_params *p, const double *w_xy,
     jobs[t].p = p;
     jobs[t].w_xy = w_xy;
     jobs[t].vrow0 = row_begin;
+    jobs[t].col0 = col_begin;
+    jobs[t].col1 = col_end;
     jobs[t].crow_begin = row_begin + rows * t / nthreads;
     jobs[t].crow_end = row_begin + rows * (t + 1) / nthreads;
     jobs[t].acc = part + npx * (size_t)t;
@@ -361,20 +368,43 @@ int or_map_from_vertices(const or_params *p, const double *w_xy,
   return 0;
 }
 
-int or_map(const or_params *p, int64_t n_stars, const double *masses,
-           const double *pos_xy, int64_t row_begin, int64_t row_end,
-           double *mu_out, double *acc_out, or_map_stats *stats, int nthreads) {
+int or_map_from_vertices(const or_params *p, const double *w_xy,
+                         int64_t row_begin, int64_t row_end,
+                         double *mu_out, double *acc_out, or_map_stats *stats,
+                         int nthreads) {
+  return map_tile_from_vertices(p, w_xy, row_begin, row_end, 0, p->n[0] - 1, mu_out,
+                                acc_out, stats, nthreads);
+}
+
+int or_map_tile(const or_params *p, int64_t n_stars, const double *masses,
+                const double *pos_xy, int64_t row_begin, int64_t row_end,
+                int64_t col_begin, int64_t col_end, double *mu_out, double *acc_out,
+                or_map_stats *stats, int nthreads) {
   if (row_end <= 0) {
     row_begin = 0;
     row_end = p->n[1] - 1;
   }
+  if (col_end <= 0) {
+    col_begin = 0;
+    col_end = p->n[0] - 1;
+  }
   if (row_begin < 0 || row_end <= row_begin || row_end > p->n[1] - 1) return -1;
-  int64_t nv = (row_end - row_begin + 1) * p->n[0];
+  if (col_begin < 0 || col_end <= col_begin || col_end > p->n[0] - 1) return -1;
+  int64_t width = col_end - col_begin + 1;
+  int64_t nv = (row_end - row_begin + 1) * width;
   double *w = (double *)malloc((size_t)nv * 2 * sizeof(double));
   if (!w) return -1;
-  run_deflect(p, n_stars, masses, pos_xy, nv, NULL, row_begin, w, nthreads);
-  int rc = or_map_from_vertices(p, w, row_begin, row_end, mu_out, acc_out, stats,
-                                nthreads);
+  run_deflect(p, n_stars, masses, pos_xy, nv, NULL, row_begin, col_begin, width, w,
+              nthreads);
+  int rc = map_tile_from_vertices(p, w, row_begin, row_end, col_begin, col_end, mu_out,
+                                  acc_out, stats, nthreads);
   free(w);
   return rc;
+}
+
+int or_map(const or_params *p, int64_t n_stars, const double *masses,
+           const double *pos_xy, int64_t row_begin, int64_t row_end,
+           double *mu_out, double *acc_out, or_map_stats *stats, int nthreads) {
+  return or_map_tile(p, n_stars, masses, pos_xy, row_begin, row_end, 0, 0, mu_out, acc_out,
+                     stats, nthreads);
 }

@@ -84,6 +84,13 @@ int or_map(const or_params *p, int64_t n_stars, const double *masses,
            const double *pos_xy, int64_t row_begin, int64_t row_end,
            double *mu_out, double *acc_out, or_map_stats *stats, int nthreads);
 
+/* Map of the tile of cells rows [row_begin, row_end) x columns
+ * [col_begin, col_end) (col_end <= 0: all columns). */
+int or_map_tile(const or_params *p, int64_t n_stars, const double *masses,
+                const double *pos_xy, int64_t row_begin, int64_t row_end,
+                int64_t col_begin, int64_t col_end, double *mu_out, double *acc_out,
+                or_map_stats *stats, int nthreads);
+
 /* Same as or_map but from precomputed source positions w_xy of the vertices
  * of rows [row_begin, row_end] (inclusive), (row_end-row_begin+1)*n[0] points. */
 int or_map_from_vertices(const or_params *p, const double *w_xy,

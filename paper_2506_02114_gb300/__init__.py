@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("img_half", ctypes.c_double * 2), ("ray_grid", ctypes.c_int64 * 2),
                 ("flux_fraction_f", ctypes.c_double), ("center_y", ctypes.c_double * 2),
                 ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
-                ("rows_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("rows_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("col_begin", ctypes.c_int64), ("col_end", ctypes.c_int64)]
 
 
 class Params(ctypes.Structure):
@@ -69,7 +70,7 @@ class Stats(ctypes.Structure):
                 ("mean_near_stars", ctypes.c_double), ("rays", ctypes.c_int64),
                 ("cells", ctypes.c_int64), ("triangles_dropped", ctypes.c_int64),
                 ("triangles_clipped", ctypes.c_int64), ("triangles_quad", ctypes.c_int64),
-                ("triangles_strip", ctypes.c_int64), ("triangles_span", ctypes.c_int64),
+                ("triangles_box", ctypes.c_int64), ("triangles_rows", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ms_tree", ctypes.c_double),
                 ("ms_expansions", ctypes.c_double), ("ms_shoot", ctypes.c_double),
                 ("ms_normalize", ctypes.c_double), ("ms_total", ctypes.c_double)]
@@ -159,7 +160,7 @@ def _ptr(a):
 
 def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=None,
                  flux_fraction_f=0.0, center_y=(0.0, 0.0), row_begin=0, row_end=0,
-                 rows_per_item=0):
+                 rows_per_item=0, col_begin=0, col_end=0):
     o = Options()
     o.mode = int(mode)
     o.time_stages = 1 if time_stages else 0
@@ -171,6 +172,7 @@ def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=No
     o.center_y[0], o.center_y[1] = float(center_y[0]), float(center_y[1])
     o.row_begin, o.row_end = int(row_begin), int(row_end)
     o.rows_per_item = int(rows_per_item)
+    o.col_begin, o.col_end = int(col_begin), int(col_end)
     return o
 
 

@@ -123,6 +123,7 @@ struct mm_map {
   int64_t N = 0;
   double R0 = 1.0;
   int64_t row_lo = 0, row_hi = 0;  // cell rows [row_lo, row_hi)
+  int64_t col_lo = 0, col_hi = 0;  // cell columns [col_lo, col_hi)
   int rows_per_item = 64;
   cudaStream_t plan_stream = nullptr;
   cudaStream_t last_stream = nullptr;
@@ -389,8 +390,8 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
   }
   LCH(launch_axis_cells(P.x0[0], P.h[0], P.n[0], h->R0, h->col_cell.p, st));
   LCH(launch_axis_cells(P.x0[1], P.h[1], P.n[1], h->R0, h->row_cell.p, st));
-  LCH(launch_active_flags(T, nn, h->col_cell.p, P.n[0], h->row_cell.p, h->row_lo, h->row_hi,
-                         h->node_act.p, h->leaf_flag.p, st));
+  LCH(launch_active_flags(T, nn, h->col_cell.p, h->col_lo, h->col_hi, h->row_cell.p, h->row_lo,
+                          h->row_hi, h->node_act.p, h->leaf_flag.p, st));
   CKS(cub_call(h, plan, [&](void *tmp, size_t &bytes) {
     return cub::DeviceScan::ExclusiveSum(tmp, bytes, h->leaf_flag.p, h->leaf_scan.p, (int)nn, st);
   }));
@@ -491,9 +492,9 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
   if (plan) {
     // lookup grid over the active cell rectangle, as deep as 4M entries allow
     cudaError_t e;
-    int CX0 = read_scalar(h->col_cell.p, st, e);
+    int CX0 = read_scalar(h->col_cell.p + h->col_lo, st, e);
     CK(e);
-    int CX1 = read_scalar(h->col_cell.p + (P.n[0] - 1), st, e);
+    int CX1 = read_scalar(h->col_cell.p + h->col_hi, st, e);
     CK(e);
     int CY0 = read_scalar(h->row_cell.p + h->row_lo, st, e);
     CK(e);
@@ -527,7 +528,9 @@ static void fill_mapdev(mm_map *h) {
   M.n1 = P.n[1];
   M.row_begin = h->row_lo;
   M.row_end = h->row_hi;
-  M.strips = (int32_t)((P.n[0] - 1 + MM_STRIP - 1) / MM_STRIP);
+  M.col_begin = h->col_lo;
+  M.col_end = h->col_hi;
+  M.strips = (int32_t)((h->col_hi - h->col_lo + MM_STRIP - 1) / MM_STRIP);
   M.rows_per_item = h->rows_per_item;
   M.row_blocks = (h->row_hi - h->row_lo + h->rows_per_item - 1) / h->rows_per_item;
   M.work_begin = 0;
@@ -627,10 +630,11 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     C.lox = P.center_y[0] - P.half_length;
     C.loy = P.center_y[1] - P.half_length;
     C.delta = P.delta;
-    LCH(launch_direct64_vertices(h->sx.p, h->sy.p, h->sm.p, h->N, C, P.n[0], h->row_lo,
-                                h->row_hi, h->verts.p, st));
-    LCH(launch_ipm_vertices(h->d_md.p, h->verts.p, P.n[0], h->row_lo, h->row_hi,
-                           h->counter.p, h->err.p, shoot_grid(), st));
+    LCH(launch_direct64_vertices(h->sx.p, h->sy.p, h->sm.p, h->N, C, h->col_lo,
+                                 h->col_hi - h->col_lo + 1, h->row_lo, h->row_hi, h->verts.p,
+                                 st));
+    LCH(launch_ipm_vertices(h->d_md.p, h->verts.p, h->col_hi - h->col_lo + 1, h->row_lo,
+                            h->row_hi, h->counter.p, h->err.p, shoot_grid(), st));
   } else {
     CKS(prepare(h, st));
     CKS(record(h, 2, st));
@@ -698,6 +702,17 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
     h->row_lo = h->opt.row_begin;
     h->row_hi = h->opt.row_end;
   }
+  // cell-column band
+  const int64_t cols = P.n[0] - 1;
+  h->col_lo = 0;
+  h->col_hi = cols;
+  if (h->opt.col_begin != 0 || h->opt.col_end != 0) {
+    if (h->opt.col_begin < 0 || h->opt.col_end <= h->opt.col_begin || h->opt.col_end > cols)
+      return fail(MM_EINVAL, "column band [%lld, %lld) outside [0, %lld)",
+                  (long long)h->opt.col_begin, (long long)h->opt.col_end, (long long)cols);
+    h->col_lo = h->opt.col_begin;
+    h->col_hi = h->opt.col_end;
+  }
 
   // star extent, coverage and root square
   double ext = 0.0, bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
@@ -753,7 +768,7 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
                          st));
     LCH(launch_gather_stars(h->pos_in.p, h->m_in.p, h->idx.p, n_stars, h->sx.p, h->sy.p, h->sm.p,
                            st));
-    CK(h->verts.ensure((size_t)P.n[0] * (h->row_hi - h->row_lo + 1)));
+    CK(h->verts.ensure((size_t)(h->col_hi - h->col_lo + 1) * (h->row_hi - h->row_lo + 1)));
     CK(cudaStreamSynchronize(st));
   } else {
     CKS(run_tree(h, st, true));
@@ -949,8 +964,8 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
   out->active_leaves = h->n_active;
   out->root_half_length = h->R0;
   out->min_leaf_half_length = h->min_leaf_L;
-  out->rays = h->P.n[0] * (h->row_hi - h->row_lo + 1);
-  out->cells = (h->P.n[0] - 1) * (h->row_hi - h->row_lo);
+  out->rays = (h->col_hi - h->col_lo + 1) * (h->row_hi - h->row_lo + 1);
+  out->cells = (h->col_hi - h->col_lo) * (h->row_hi - h->row_lo);
   out->ms_tree = out->ms_expansions = out->ms_shoot = out->ms_normalize = out->ms_total = -1.0;
   if (h->last_stream || h->ran) CK(cudaStreamSynchronize(h->last_stream));
   if (h->mode == MM_FMM_FP32 && h->n_nodes > 0) {
@@ -982,8 +997,8 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
     out->triangles_dropped = (int64_t)st[0];
     out->triangles_clipped = (int64_t)st[1];
     out->triangles_quad = (int64_t)st[2];
-    out->triangles_strip = (int64_t)st[3];
-    out->triangles_span = (int64_t)st[4];
+    out->triangles_box = (int64_t)st[3];
+    out->triangles_rows = (int64_t)st[4];
   }
   out->kernel_launches = h->launches;
   if (h->ev_recorded) {

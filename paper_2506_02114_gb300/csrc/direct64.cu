@@ -58,11 +58,12 @@ __device__ __forceinline__ void lens64(const DirectConst &C, double x, double y,
 
 __global__ void __launch_bounds__(D64_TILE) k_direct64_vertices(
     const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sm,
-    int64_t n_stars, DirectConst C, int64_t n0, int64_t row_lo, int64_t row_hi, Vtx *out) {
-  const int64_t nv = n0 * (row_hi - row_lo + 1);
+    int64_t n_stars, DirectConst C, int64_t col0, int64_t width, int64_t row_lo, int64_t row_hi,
+    Vtx *out) {
+  const int64_t nv = width * (row_hi - row_lo + 1);
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t tt = t < nv ? t : nv - 1;
-  const int64_t i = tt % n0, j = row_lo + tt / n0;
+  const int64_t i = col0 + tt % width, j = row_lo + tt / width;
   const double x = __dadd_rn(C.x0, __dmul_rn((double)i, C.hx));
   const double y = __dadd_rn(C.y0, __dmul_rn((double)j, C.hy));
   double ax, ay, wx, wy;
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(D64_TILE) k_direct64_vertices(
     o.px = o.py = MM_VTX_INVALID;
     o.fx = o.fy = 0.f;
   } else {
-    u = fmin(fmax(u, -536870912.0), 536870912.0);
+    u = fmin(fmax(u, -536870912.0), 536870912.0);  // pixel indices within +-2^29
     v = fmin(fmax(v, -536870912.0), 536870912.0);
     const double fu = floor(u), fv = floor(v);
     o.px = (int)fu;
@@ -117,8 +118,11 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
                                                       unsigned long long *work_counter,
                                                       unsigned *err) {
   const int lane = threadIdx.x & 31;
-  __shared__ SmallTri s_queue[8][64];
-  WarpQueue wq = {s_queue[threadIdx.x >> 5], 0};
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
+  WarpQueue wq = {ws->quad, 0};
+  JobQueue jp = {ws->pix, 0};
+  JobQueue jr = {ws->rows, 0};
   const MapDev &M = maps[0];
   const int64_t strips = (n0 - 1 + MM_STRIP - 1) / MM_STRIP;
   const int64_t rows = row_hi - row_lo;  // cell rows
@@ -158,12 +162,15 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
                                                  tri ? cur : cur_r, ra, cnt, se, job)
                                   : TRI_DONE;
         wq_push(M, wq, code == TRI_SMALL, se, lane);
-        warp_row_jobs(M, code == TRI_ROWS, job, lane);
+        jq_push<false>(M, jp, code == TRI_PIX, job, lane);
+        jq_push<true>(M, jr, code == TRI_ROWS, job, lane);
       }
       prev = cur;
     }
     run_flush(M, ra);
     wq_drain(M, wq, lane);
+    jq_drain<false>(M, jp, lane);
+    jq_drain<true>(M, jr, lane);
   }
   unsigned long long v[5] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big};
 #pragma unroll
@@ -174,13 +181,13 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
 }
 
 cudaError_t launch_direct64_vertices(const double *sx, const double *sy, const double *sm,
-                                     int64_t n_stars, const DirectConst &C, int64_t n0,
-                                     int64_t row_lo, int64_t row_hi, Vtx *out,
+                                     int64_t n_stars, const DirectConst &C, int64_t col0,
+                                     int64_t width, int64_t row_lo, int64_t row_hi, Vtx *out,
                                      cudaStream_t st) {
-  const int64_t nv = n0 * (row_hi - row_lo + 1);
+  const int64_t nv = width * (row_hi - row_lo + 1);
   if (nv <= 0) return cudaSuccess;
   k_direct64_vertices<<<(unsigned)((nv + D64_TILE - 1) / D64_TILE), D64_TILE, 0, st>>>(
-      sx, sy, sm, n_stars, C, n0, row_lo, row_hi, out);
+      sx, sy, sm, n_stars, C, col0, width, row_lo, row_hi, out);
   return cudaGetLastError();
 }
 
@@ -197,7 +204,11 @@ cudaError_t launch_ipm_vertices(const MapDev *d_map, const Vtx *verts, int64_t n
                                 int64_t row_lo, int64_t row_hi, unsigned long long *counter,
                                 unsigned *err, int grid, cudaStream_t st) {
   if (row_hi <= row_lo || n0 < 2) return cudaSuccess;
-  k_ipm_vertices<<<grid, 256, 0, st>>>(d_map, verts, n0, row_lo, row_hi, counter, err);
+  const int smem = (int)MM_SHOOT_SMEM_BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_ipm_vertices, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+  if (e != cudaSuccess) return e;
+  k_ipm_vertices<<<grid, 256, smem, st>>>(d_map, verts, n0, row_lo, row_hi, counter, err);
   return cudaGetLastError();
 }
 

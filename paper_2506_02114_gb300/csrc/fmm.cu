@@ -271,8 +271,9 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_active,
   const double Wx = (ak + C.gamma) * zx - c1.x / L;
   const double Wy = (ak - C.gamma) * zy + c1.y / L;  // - conj(c1/L)
   double U = (Wx - C.lox) / C.delta, V = (Wy - C.loy) / C.delta;
-  U = fmin(fmax(U, -1.0e9), 1.0e9);
-  V = fmin(fmax(V, -1.0e9), 1.0e9);
+  // |Ui|, |Vi| < 2^28 keeps vertex pixel indices within +-2^29
+  U = fmin(fmax(U, -2.0e8), 2.0e8);
+  V = fmin(fmax(V, -2.0e8), 2.0e8);
   const double Ui = floor(U), Vi = floor(V);
   R.Ui = (int32_t)Ui;
   R.Vi = (int32_t)Vi;

@@ -29,6 +29,9 @@
 //   * it spans at most 2 x 2 pixels: queued per warp in shared memory and
 //     apportioned 32 at a time from three quadrant areas by
 //     inclusion-exclusion;
+//   * its box holds at most MM_MED_PIXELS pixels of the map: the pixels of
+//     all such triangles of a warp are dealt out to its lanes, one pixel
+//     (one box area) per lane at a time;
 //   * larger (cells next to a star map to triangles hundreds of pixels
 //     wide): the pixel rows of all such triangles of a warp are dealt out to
 //     its lanes; each row adds the constant 1/|area| to its run of fully
@@ -52,10 +55,12 @@ __device__ __forceinline__ float rcp_approx_f(float x) {
   return y;
 }
 
-// Share of a triangle in fixed-point units (2^32 = the whole triangle).
+// Share of a triangle in fixed-point units (2^32 = the whole triangle).  An
+// FP32 fraction carries 24 significant bits, so it is rounded at 2^-24 and
+// shifted: 32-bit conversions only (64-bit ones would run on the FP64 pipe).
 __device__ __forceinline__ unsigned long long frac_to_fixed(float f) {
   f = fminf(fmaxf(f, 0.0f), 1.0f);
-  return __float2ull_rn(f * 4294967296.0f);
+  return (unsigned long long)__float2uint_rn(f * 16777216.0f) << 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -204,8 +209,8 @@ struct WarpQueue {
   int n;
 };
 
-__device__ __forceinline__ void wq_push(const MapDev &M, WarpQueue &wq,
-                                        bool want, const SmallTri &e, int lane) {
+__device__ __forceinline__ void wq_push(const MapDev &M, WarpQueue &wq, bool want,
+                                        const SmallTri &e, int lane) {
   const unsigned m = __ballot_sync(0xffffffffu, want);
   if (!m) return;
   const int pos = wq.n + __popc(m & ((1u << lane) - 1u));
@@ -220,8 +225,7 @@ __device__ __forceinline__ void wq_push(const MapDev &M, WarpQueue &wq,
   }
 }
 
-__device__ __forceinline__ void wq_drain(const MapDev &M, WarpQueue &wq,
-                                         int lane) {
+__device__ __forceinline__ void wq_drain(const MapDev &M, WarpQueue &wq, int lane) {
   if (wq.n > 0) {
     SmallTri t;
     const bool have = lane < wq.n;
@@ -238,25 +242,28 @@ __device__ __forceinline__ void wq_drain(const MapDev &M, WarpQueue &wq,
 // ---------------------------------------------------------------------------
 
 // Per-lane triangle counters, reduced per warp into MapDev::stat:
-// [0] dropped, [1] multi-pixel (clipped) in the map, [2] queued 2x2,
-// [3] row jobs with a box of at most MM_BIG_PIXELS pixels, [4] larger ones.
+// [0] dropped, [1] multi-pixel (clipped) in the map, [2] within a 2 x 2 box,
+// [3] box of at most MM_MED_PIXELS pixels (pixel jobs), [4] larger (row jobs).
 struct IpmCounters {
   unsigned long long dropped, clipped, small, strip, big;
 };
 
-// A triangle handed to the whole warp: frame pixel and frame coordinates.
-struct TriJob {
+// A triangle shared out to the whole warp: frame pixel and frame coordinates.
+struct __align__(16) TriJob {
   int ox, oy;
   float t[6];
   float inv2;  // 2 / signed area
+  int pad[3];
 };
 
-enum { TRI_DONE = 0, TRI_SMALL = 1, TRI_ROWS = 2 };
+enum { TRI_DONE = 0, TRI_SMALL = 1, TRI_PIX = 2, TRI_ROWS = 3 };
 
 // Apportion one triangle (a, b, c).  One-pixel triangles are finished here;
-// returns TRI_SMALL (se filled) for a triangle within a 2 x 2 pixel box, to
-// be pushed on the warp queue, and TRI_ROWS (job filled) for a larger one,
-// whose pixel rows the whole warp shares out (warp_row_jobs).
+// returns TRI_SMALL (se filled) for a triangle within a 2 x 2 pixel box, to be
+// pushed on the warp queue, TRI_PIX (job filled) when its box within the map
+// holds at most MM_MED_PIXELS pixels, which the warp deals out one pixel per
+// lane (warp_pixel_jobs), and TRI_ROWS (job filled) for a larger one, whose
+// pixel rows the warp deals out (warp_row_jobs).
 __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
                                             const Vtx &b, const Vtx &c, RunAcc &ra,
                                             IpmCounters &cnt, SmallTri &se, TriJob &job) {
@@ -268,10 +275,11 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   float t[6];
   t[0] = a.fx;
   t[1] = a.fy;
-  t[2] = (float)((long long)b.px - ox) + b.fx;
-  t[3] = (float)((long long)b.py - oy) + b.fy;
-  t[4] = (float)((long long)c.px - ox) + c.fx;
-  t[5] = (float)((long long)c.py - oy) + c.fy;
+  // pixel indices stay within +-2^29, so differences fit in 32 bits
+  t[2] = (float)(b.px - ox) + b.fx;
+  t[3] = (float)(b.py - oy) + b.fy;
+  t[4] = (float)(c.px - ox) + c.fx;
+  t[5] = (float)(c.py - oy) + c.fy;
   const float area2 = (t[2] - t[0]) * (t[5] - t[1]) - (t[4] - t[0]) * (t[3] - t[1]);
   if (!(area2 != 0.f) || !isfinite(area2)) {
     cnt.dropped++;
@@ -313,10 +321,11 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
 #pragma unroll
   for (int k = 0; k < 6; k++) job.t[k] = t[k];
   job.inv2 = 2.0f / area2;
-  if ((ch - cl + 1) * (rh - rl + 1) > MM_BIG_PIXELS)
-    cnt.big++;
-  else
+  if ((ch - cl + 1) * (rh - rl + 1) <= MM_MED_PIXELS) {
     cnt.strip++;
+    return TRI_PIX;
+  }
+  cnt.big++;
   return TRI_ROWS;
 }
 
@@ -372,16 +381,16 @@ __device__ __forceinline__ void span_row(const MapDev &M, const TriJob &J,
     if (vy >= y0 && vy <= y1) bx0 = fminf(bx0, J.t[2 * k]), bx1 = fmaxf(bx1, J.t[2 * k]);
   }
   if (!(bx0 <= bx1)) return;
-  long long c0 = (long long)floorf(fmaxf(bx0, -1.0e9f));
-  long long c1 = (long long)floorf(fminf(bx1, 1.0e9f));
+  long long c0 = (int)floorf(fmaxf(bx0, -1.0e9f));
+  long long c1 = (int)floorf(fminf(bx1, 1.0e9f));
   if (c0 < cl) c0 = cl;
   if (c1 > ch) c1 = ch;
   if (c0 > c1) return;
   long long fa = 1, fb = 0;  // fully covered columns [fa, fb]
   if (s0 && s1) {
     const float eps = 1e-3f;
-    fa = (long long)ceilf(fmaxf(l0, l1) + eps);
-    fb = (long long)floorf(fminf(r0, r1) - eps) - 1;
+    fa = (int)ceilf(fminf(fmaxf(l0, l1) + eps, 1.0e9f));
+    fb = (long long)(int)floorf(fmaxf(fminf(r0, r1) - eps, -1.0e9f)) - 1;
     if (fa < c0) fa = c0;
     if (fb > c1) fb = c1;
   }
@@ -406,8 +415,8 @@ __device__ __forceinline__ void span_row(const MapDev &M, const TriJob &J,
 // lanes, one row per lane at a time.  A lane finds the triangle owning its
 // row by binary search over the warp's inclusive scan of row counts and
 // takes that triangle from its owner by shuffles.  Call with all 32 lanes.
-__device__ __forceinline__ void warp_row_jobs(const MapDev &M, bool have,
-                                              const TriJob &job, int lane) {
+static __device__ __noinline__ void warp_row_jobs(const MapDev &M, bool have, const TriJob &job,
+                                           int lane) {
   if (!__any_sync(0xffffffffu, have)) return;
   int rl = 0, nrows = 0, cl = 0, ch = -1;
   if (have) {
@@ -415,10 +424,10 @@ __device__ __forceinline__ void warp_row_jobs(const MapDev &M, bool have,
     const float ymax = fmaxf(job.t[1], fmaxf(job.t[3], job.t[5]));
     const float xmin = fminf(job.t[0], fminf(job.t[2], job.t[4]));
     const float xmax = fmaxf(job.t[0], fmaxf(job.t[2], job.t[4]));
-    long long r0 = (long long)floorf(fmaxf(ymin, -1.0e9f));
-    long long r1 = (long long)floorf(fminf(ymax, 1.0e9f));
-    long long c0 = (long long)floorf(fmaxf(xmin, -1.0e9f));
-    long long c1 = (long long)floorf(fminf(xmax, 1.0e9f));
+    long long r0 = (int)floorf(fmaxf(ymin, -1.0e9f));
+    long long r1 = (int)floorf(fminf(ymax, 1.0e9f));
+    long long c0 = (int)floorf(fmaxf(xmin, -1.0e9f));
+    long long c1 = (int)floorf(fminf(xmax, 1.0e9f));
     if (r0 < -(long long)job.oy) r0 = -(long long)job.oy;
     if (r1 > (long long)M.npix - 1 - job.oy) r1 = (long long)M.npix - 1 - job.oy;
     if (c0 < -(long long)job.ox) c0 = -(long long)job.ox;
@@ -461,11 +470,124 @@ __device__ __forceinline__ void warp_row_jobs(const MapDev &M, bool have,
     const int kn = __shfl_sync(0xffffffffu, nrows, k);
     const int kincl = __shfl_sync(0xffffffffu, incl, k);
     if (task < total) {
-      const unsigned long long full =
-          (unsigned long long)llrint(fabs((double)J.inv2) * 4294967296.0);
+      // a fully covered pixel holds 1/|area| of the triangle (< 1 when any does)
+      const unsigned long long full = frac_to_fixed(fabsf(J.inv2));
       span_row(M, J, krl + (task - (kincl - kn)), kcl, kch, full);
     }
   }
+}
+
+// Lanes whose `have` is set hold a triangle whose box (within the map) holds
+// at most MM_MED_PIXELS pixels; all those pixels are dealt out to the 32
+// lanes, one per lane at a time, and each lane adds its pixel's share.
+static __device__ __noinline__ void warp_pixel_jobs(const MapDev &M, bool have, const TriJob &job,
+                                             int lane) {
+  if (!__any_sync(0xffffffffu, have)) return;
+  int c0 = 0, r0 = 0, w = 1, npx = 0;
+  if (have) {
+    const float xmin = fminf(job.t[0], fminf(job.t[2], job.t[4]));
+    const float xmax = fmaxf(job.t[0], fmaxf(job.t[2], job.t[4]));
+    const float ymin = fminf(job.t[1], fminf(job.t[3], job.t[5]));
+    const float ymax = fmaxf(job.t[1], fmaxf(job.t[3], job.t[5]));
+    int cl = (int)floorf(xmin), ch = (int)floorf(xmax);
+    int rl = (int)floorf(ymin), rh = (int)floorf(ymax);
+    cl = max(cl, -job.ox);
+    ch = min(ch, M.npix - 1 - job.ox);
+    rl = max(rl, -job.oy);
+    rh = min(rh, M.npix - 1 - job.oy);
+    c0 = cl;
+    r0 = rl;
+    w = ch - cl + 1;
+    npx = (ch >= cl && rh >= rl) ? w * (rh - rl + 1) : 0;
+  }
+  int incl = npx;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  for (int base = 0; base < total; base += 32) {
+    const int task = base + lane;
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int it = 0; it < 5; it++) {
+      const int mid = (lo + hi) >> 1;
+      if (__shfl_sync(0xffffffffu, incl, mid) > task)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    const int k = lo;
+    float t[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) t[q] = __shfl_sync(0xffffffffu, job.t[q], k);
+    const int kox = __shfl_sync(0xffffffffu, job.ox, k);
+    const int koy = __shfl_sync(0xffffffffu, job.oy, k);
+    const float kinv = __shfl_sync(0xffffffffu, job.inv2, k);
+    const int kc0 = __shfl_sync(0xffffffffu, c0, k);
+    const int kr0 = __shfl_sync(0xffffffffu, r0, k);
+    const int kw = __shfl_sync(0xffffffffu, w, k);
+    const int kstart = __shfl_sync(0xffffffffu, incl - npx, k);
+    if (task < total) {
+      const int q = task - kstart;
+      const int c = kc0 + q % kw, r = kr0 + q / kw;
+      deposit(M, (long long)kox + c, (long long)koy + r,
+              frac_to_fixed(pixel_fraction(t, c, r, kinv)));
+    }
+  }
+}
+
+// Per-warp queue of triangles for the pixel (PIX) or row (ROWS) jobs, in
+// shared memory (capacity 64 >= 31 + 31 + 2).  A full batch of 32 is shared
+// out at once, so the lanes stay busy and the dealing overhead is amortised.
+struct JobQueue {
+  TriJob *q;
+  int n;
+};
+
+// Shared memory of one warp: the three queues.
+struct WarpSmem {
+  SmallTri quad[64];
+  TriJob pix[64];
+  TriJob rows[64];
+};
+#define MM_SHOOT_SMEM_BYTES (8 * sizeof(WarpSmem))  // 8 warps per block
+
+template <bool ROWS>
+__device__ __forceinline__ void jq_push(const MapDev &M, JobQueue &jq, bool want,
+                                        const TriJob &job, int lane) {
+  const unsigned m = __ballot_sync(0xffffffffu, want);
+  if (!m) return;
+  const int pos = jq.n + __popc(m & ((1u << lane) - 1u));
+  if (want) jq.q[pos] = job;
+  jq.n += __popc(m);
+  __syncwarp();
+  while (jq.n >= 32) {
+    const TriJob t = jq.q[jq.n - 32 + lane];
+    __syncwarp();
+    jq.n -= 32;
+    if (ROWS)
+      warp_row_jobs(M, true, t, lane);
+    else
+      warp_pixel_jobs(M, true, t, lane);
+  }
+}
+
+template <bool ROWS>
+__device__ __forceinline__ void jq_drain(const MapDev &M, JobQueue &jq, int lane) {
+  if (jq.n > 0) {
+    const bool have = lane < jq.n;
+    TriJob t;
+    if (have) t = jq.q[lane];
+    __syncwarp();
+    jq.n = 0;
+    if (ROWS)
+      warp_row_jobs(M, have, t, lane);
+    else
+      warp_pixel_jobs(M, have, t, lane);
+  }
+  __syncwarp();
 }
 
 }  // namespace mm

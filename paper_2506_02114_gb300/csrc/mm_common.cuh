@@ -12,8 +12,8 @@
 #define MM_DMAX 21            // deepest quadtree level
 #define MM_PMAX 64            // largest expansion order accepted by the ABI
 #define MM_STRIP 31           // cell columns per warp work item (32 vertex columns)
-#define MM_BIG_PIXELS 32      // bbox area (in pixels, inside the map) above which a
-                              // triangle is apportioned by the whole warp, row by row
+#define MM_MED_PIXELS 64      // bounding box (pixels) up to which a triangle is
+                              // apportioned from quadrant areas by one lane
 
 namespace mm {
 
@@ -57,6 +57,7 @@ struct MapDev {
   // ray grid
   int64_t n0, n1;             // vertices per axis
   int64_t row_begin, row_end; // cell rows [row_begin, row_end)
+  int64_t col_begin, col_end; // cell columns [col_begin, col_end)
   int32_t strips, rows_per_item;
   int64_t row_blocks;
   int64_t work_begin;         // first global work item of this map

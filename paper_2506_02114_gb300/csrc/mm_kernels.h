@@ -45,9 +45,9 @@ cudaError_t launch_axis_cells(double x0, double h, int64_t n, double R0, int32_t
 // flags[node] = 1 for active leaves (leaf containing ray vertices); also
 // node_act[node] = 1 for every active node
 cudaError_t launch_active_flags(const TreeDev &T, int64_t n_nodes, const int32_t *col_cell,
-                                int64_t n0, const int32_t *row_cell, int64_t row_lo,
-                                int64_t row_hi, int32_t *node_act, int32_t *leaf_flag,
-                                cudaStream_t st);
+                                int64_t col_lo, int64_t col_hi, const int32_t *row_cell,
+                                int64_t row_lo, int64_t row_hi, int32_t *node_act,
+                                int32_t *leaf_flag, cudaStream_t st);
 cudaError_t launch_compact_leaves(int64_t n_nodes, const int32_t *leaf_flag,
                                   const int32_t *leaf_scan, int32_t *node_active,
                                   int32_t *active_list, cudaStream_t st);
@@ -96,14 +96,15 @@ struct DirectConst {
   double x0, y0, hx, hy;
   double lox, loy, delta;
 };
+// vertices of columns [col0, col0 + width) and rows [row_lo, row_hi], row-major
 cudaError_t launch_direct64_vertices(const double *sx, const double *sy, const double *sm,
-                                     int64_t n_stars, const DirectConst &C, int64_t n0,
-                                     int64_t row_lo, int64_t row_hi, Vtx *out,
+                                     int64_t n_stars, const DirectConst &C, int64_t col0,
+                                     int64_t width, int64_t row_lo, int64_t row_hi, Vtx *out,
                                      cudaStream_t st);
 cudaError_t launch_direct64_points(const double *sx, const double *sy, const double *sm,
                                    int64_t n_stars, const DirectConst &C, int64_t n,
                                    const double *z, double *w, cudaStream_t st);
-cudaError_t launch_ipm_vertices(const MapDev *d_map, const Vtx *verts, int64_t n0,
+cudaError_t launch_ipm_vertices(const MapDev *d_map, const Vtx *verts, int64_t width,
                                 int64_t row_lo, int64_t row_hi, unsigned long long *counter,
                                 unsigned *err, int grid, cudaStream_t st);
 

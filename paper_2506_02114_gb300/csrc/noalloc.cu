@@ -138,6 +138,8 @@ extern "C" mm_status mm_map_plain_fp64_noalloc(
   md.n1 = n1;
   md.row_begin = 0;
   md.row_end = n1 - 1;
+  md.col_begin = 0;
+  md.col_end = n0 - 1;
   md.rows_per_item = 64;
   md.npix = npix;
   md.acc = acc;
@@ -161,7 +163,7 @@ extern "C" mm_status mm_map_plain_fp64_noalloc(
   }
   k_write_mapdev<<<1, 1, 0, st>>>(md, d_md);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(MM_ECUDA, "map descriptor", e);
-  if ((e = launch_direct64_vertices(sx, sy, sm, n_stars, C, n0, 0, n1 - 1, verts, st)) !=
+  if ((e = launch_direct64_vertices(sx, sy, sm, n_stars, C, 0, n0, 0, n1 - 1, verts, st)) !=
       cudaSuccess)
     return fail(MM_ECUDA, "direct-sum deflection", e);
   int sms = 0;

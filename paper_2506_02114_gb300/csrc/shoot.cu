@@ -64,24 +64,48 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
   }
 
   // near field: S = sum m g / |g|^2 in grid units (|g|^2 = gx^2 + rho gy^2)
-  float Sx = 0.f, Sy = 0.f;
+  // two stars per iteration into two accumulator pairs (independent chains)
+  float Sx = 0.f, Sy = 0.f, Sx2 = 0.f, Sy2 = 0.f;
   const int maxcnt = __reduce_max_sync(0xffffffffu, near_cnt);
-  for (int k = 0; k < maxcnt; k++) {
-    if (k < near_cnt) {
-      const float4 s = __ldg(reinterpret_cast<const float4 *>(M.near_pos) + near_off + k);
-      const float m = __ldg(M.near_m + near_off + k);
-      float dx = (fi - s.x) - s.y;  // (i - i_ref - Kx) - fx: exact near the star
-      float dy = (fj - s.z) - s.w;
-      if (FRAC) {
-        dx += ti;
-        dy += tj;
-      }
-      float r2 = SQUARE ? fmaf(dx, dx, dy * dy) : fmaf(dx, dx, M.rho * dy * dy);
-      float qq = m * rcp_approx(r2);
-      Sx = fmaf(qq, dx, Sx);
-      Sy = fmaf(qq, dy, Sy);
+  const float4 *np_ = reinterpret_cast<const float4 *>(M.near_pos) + near_off;
+  const float *nm_ = M.near_m + near_off;
+  int k = 0;
+  for (; k + 1 < maxcnt; k += 2) {
+    const bool a0 = k < near_cnt, a1 = k + 1 < near_cnt;
+    const float4 s0 = a0 ? __ldg(np_ + k) : make_float4(0.f, 1.f, 0.f, 0.f);
+    const float4 s1 = a1 ? __ldg(np_ + k + 1) : make_float4(0.f, 1.f, 0.f, 0.f);
+    const float m0 = a0 ? __ldg(nm_ + k) : 0.f, m1 = a1 ? __ldg(nm_ + k + 1) : 0.f;
+    float dx0 = (fi - s0.x) - s0.y, dy0 = (fj - s0.z) - s0.w;
+    float dx1 = (fi - s1.x) - s1.y, dy1 = (fj - s1.z) - s1.w;
+    if (FRAC) {
+      dx0 += ti;
+      dy0 += tj;
+      dx1 += ti;
+      dy1 += tj;
     }
+    const float r0 = SQUARE ? fmaf(dx0, dx0, dy0 * dy0) : fmaf(dx0, dx0, M.rho * dy0 * dy0);
+    const float r1 = SQUARE ? fmaf(dx1, dx1, dy1 * dy1) : fmaf(dx1, dx1, M.rho * dy1 * dy1);
+    const float q0 = m0 * rcp_approx(r0), q1 = m1 * rcp_approx(r1);
+    Sx = fmaf(q0, dx0, Sx);
+    Sy = fmaf(q0, dy0, Sy);
+    Sx2 = fmaf(q1, dx1, Sx2);
+    Sy2 = fmaf(q1, dy1, Sy2);
   }
+  if (k < maxcnt && k < near_cnt) {
+    const float4 s0 = __ldg(np_ + k);
+    const float m0 = __ldg(nm_ + k);
+    float dx0 = (fi - s0.x) - s0.y, dy0 = (fj - s0.z) - s0.w;
+    if (FRAC) {
+      dx0 += ti;
+      dy0 += tj;
+    }
+    const float r0 = SQUARE ? fmaf(dx0, dx0, dy0 * dy0) : fmaf(dx0, dx0, M.rho * dy0 * dy0);
+    const float q0 = m0 * rcp_approx(r0);
+    Sx = fmaf(q0, dx0, Sx);
+    Sy = fmaf(q0, dy0, Sy);
+  }
+  Sx += Sx2;
+  Sy += Sy2;
 
   // far field: f = sum_{l=2}^{p} e_l zeta^(l-1), e_l = l c_l / (L delta)
   float fr = 0.f, fim = 0.f;
@@ -115,7 +139,7 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
     out.fy = 0.f;
     return out;
   }
-  const float lim = 536870912.0f;  // 2^29 pixels: far outside any map
+  const float lim = 268435456.0f;  // 2^28 pixels: far outside any map
   u = fminf(fmaxf(u, -lim), lim);
   v = fminf(fmaxf(v, -lim), lim);
   float flu = floorf(u), flv = floorf(v);
@@ -162,8 +186,11 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
                                                    unsigned long long *work_counter,
                                                    unsigned *err) {
   const int lane = threadIdx.x & 31;
-  __shared__ SmallTri s_queue[8][64];
-  WarpQueue wq = {s_queue[threadIdx.x >> 5], 0};
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
+  WarpQueue wq = {ws->quad, 0};
+  JobQueue jp = {ws->pix, 0};
+  JobQueue jr = {ws->rows, 0};
   IpmCounters cnt = {0, 0, 0, 0, 0};
   int last_map = -1;
   while (true) {
@@ -190,13 +217,13 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
     }
     const int64_t local = (int64_t)w - M.work_begin;
     const int64_t s = local % M.strips, b = local / M.strips;
-    const int64_t i = s * MM_STRIP + lane;
+    const int64_t i = M.col_begin + s * MM_STRIP + lane;
     const int64_t jb = M.row_begin + b * M.rows_per_item;
     int64_t je = jb + M.rows_per_item;
     if (je > M.row_end) je = M.row_end;
-    const bool vvalid = i < M.n0;
-    const int cx = __ldg(&M.col_cell[vvalid ? i : M.n0 - 1]);
-    const bool cell_col = (lane < MM_STRIP) && (i + 1 < M.n0);
+    const bool vvalid = i <= M.col_end;  // vertex columns [col_begin, col_end]
+    const int cx = __ldg(&M.col_cell[vvalid ? i : M.col_end]);
+    const bool cell_col = (lane < MM_STRIP) && (i < M.col_end);
     RunAcc ra = {LLONG_MIN, LLONG_MIN, 0ull};
     Vtx prev;
     {
@@ -219,12 +246,15 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
                                                  tri ? cur : cur_r, ra, cnt, se, job)
                                   : TRI_DONE;
         wq_push(M, wq, code == TRI_SMALL, se, lane);
-        warp_row_jobs(M, code == TRI_ROWS, job, lane);
+        jq_push<false>(M, jp, code == TRI_PIX, job, lane);
+        jq_push<true>(M, jr, code == TRI_ROWS, job, lane);
       }
       prev = cur;
     }
     run_flush(M, ra);
     wq_drain(M, wq, lane);
+    jq_drain<false>(M, jp, lane);
+    jq_drain<true>(M, jr, lane);
   }
   if (last_map >= 0) flush_counters(maps[last_map], cnt, lane);
 }
@@ -313,10 +343,17 @@ cudaError_t launch_shoot_ipm(const MapDev *d_maps, int n_maps, int64_t total_wor
                              bool square, unsigned long long *counter, unsigned *err, int grid,
                              cudaStream_t st) {
   if (total_work <= 0) return cudaSuccess;
-  if (square)
-    k_shoot_ipm<true><<<grid, 256, 0, st>>>(d_maps, n_maps, total_work, counter, err);
-  else
-    k_shoot_ipm<false><<<grid, 256, 0, st>>>(d_maps, n_maps, total_work, counter, err);
+  const int smem = (int)MM_SHOOT_SMEM_BYTES;
+  cudaError_t e;
+  if (square) {
+    e = cudaFuncSetAttribute(k_shoot_ipm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_shoot_ipm<true><<<grid, 256, smem, st>>>(d_maps, n_maps, total_work, counter, err);
+  } else {
+    e = cudaFuncSetAttribute(k_shoot_ipm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_shoot_ipm<false><<<grid, 256, smem, st>>>(d_maps, n_maps, total_work, counter, err);
+  }
   return cudaGetLastError();
 }
 

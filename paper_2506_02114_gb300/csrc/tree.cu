@@ -120,12 +120,13 @@ __global__ void k_axis_cells(double x0, double h, int64_t n, double R0, int32_t 
   out[t] = cell_of(x, R0);
 }
 
-__global__ void k_active_flags(TreeDev T, int64_t n_nodes, const int32_t *col_cell, int64_t n0,
-                               const int32_t *row_cell, int64_t row_lo, int64_t row_hi,
-                               int32_t *node_act, int32_t *leaf_flag) {
+__global__ void k_active_flags(TreeDev T, int64_t n_nodes, const int32_t *col_cell,
+                               int64_t col_lo, int64_t col_hi, const int32_t *row_cell,
+                               int64_t row_lo, int64_t row_hi, int32_t *node_act,
+                               int32_t *leaf_flag) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_nodes) return;
-  const int CX0 = col_cell[0], CX1 = col_cell[n0 - 1];
+  const int CX0 = col_cell[col_lo], CX1 = col_cell[col_hi];
   const int CY0 = row_cell[row_lo], CY1 = row_cell[row_hi];
   uint32_t cx, cy;
   morton_decode(T.code[t], cx, cy);
@@ -215,12 +216,13 @@ cudaError_t launch_axis_cells(double x0, double h, int64_t n, double R0, int32_t
 }
 
 cudaError_t launch_active_flags(const TreeDev &T, int64_t n_nodes, const int32_t *col_cell,
-                                int64_t n0, const int32_t *row_cell, int64_t row_lo,
-                                int64_t row_hi, int32_t *node_act, int32_t *leaf_flag,
-                                cudaStream_t st) {
+                                int64_t col_lo, int64_t col_hi, const int32_t *row_cell,
+                                int64_t row_lo, int64_t row_hi, int32_t *node_act,
+                                int32_t *leaf_flag, cudaStream_t st) {
   if (n_nodes <= 0) return cudaSuccess;
-  k_active_flags<<<blocks_for(n_nodes, 256), 256, 0, st>>>(T, n_nodes, col_cell, n0, row_cell,
-                                                           row_lo, row_hi, node_act, leaf_flag);
+  k_active_flags<<<blocks_for(n_nodes, 256), 256, 0, st>>>(T, n_nodes, col_cell, col_lo, col_hi,
+                                                           row_cell, row_lo, row_hi, node_act,
+                                                           leaf_flag);
   return cudaGetLastError();
 }
 
