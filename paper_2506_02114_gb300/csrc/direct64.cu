@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
     if (je > row_hi) je = row_hi;
     const bool vvalid = i < n0;
     const bool cell_col = (lane < MM_STRIP) && (i + 1 < n0);
-    RunAcc ra = {LLONG_MIN, LLONG_MIN, 0ull};
+    RunAcc ra = {-1, 0ull};
     Vtx prev = load_vtx(verts, n0, row_lo, i, jb, vvalid);
     for (int64_t j = jb + 1; j <= je; j++) {
       const Vtx cur = load_vtx(verts, n0, row_lo, i, j, vvalid);
@@ -172,11 +172,11 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
     jq_drain<false>(M, jp, lane);
     jq_drain<true>(M, jr, lane);
   }
-  unsigned long long v[5] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big};
+  unsigned v[5] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big};
 #pragma unroll
   for (int k = 0; k < 5; k++) {
     for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);
-    if (lane == 0 && v[k]) atomicAdd(&M.stat[k], v[k]);
+    if (lane == 0 && v[k]) atomicAdd(&M.stat[k], (unsigned long long)v[k]);
   }
 }
 

@@ -77,25 +77,25 @@ __device__ __forceinline__ void deposit(const MapDev &M, long long gx, long long
 // Lane-private run accumulator: consecutive one-pixel triangles of a lane's
 // column usually hit the same pixel; they are summed in a register.
 struct RunAcc {
-  long long gx, gy;
+  long long idx;  // map index of the pixel being summed, -1 for none
   unsigned long long val;
 };
 
 __device__ __forceinline__ void run_flush(const MapDev &M, RunAcc &a) {
-  if (a.val) deposit(M, a.gx, a.gy, a.val);
+  if (a.idx >= 0) atomicAdd(&M.acc[a.idx], a.val);
+  a.idx = -1;
   a.val = 0;
-  a.gx = LLONG_MIN;
 }
 
-__device__ __forceinline__ void run_add(const MapDev &M, RunAcc &a,
-                                        long long gx, long long gy, unsigned long long v) {
-  if (gx == a.gx && gy == a.gy) {
+// Add v to in-map pixel idx.
+__device__ __forceinline__ void run_add(const MapDev &M, RunAcc &a, long long idx,
+                                        unsigned long long v) {
+  if (idx == a.idx) {
     a.val += v;
     return;
   }
-  if (a.val) deposit(M, a.gx, a.gy, a.val);
-  a.gx = gx;
-  a.gy = gy;
+  if (a.idx >= 0) atomicAdd(&M.acc[a.idx], a.val);
+  a.idx = idx;
   a.val = v;
 }
 
@@ -245,7 +245,7 @@ __device__ __forceinline__ void wq_drain(const MapDev &M, WarpQueue &wq, int lan
 // [0] dropped, [1] multi-pixel (clipped) in the map, [2] within a 2 x 2 box,
 // [3] box of at most MM_MED_PIXELS pixels (pixel jobs), [4] larger (row jobs).
 struct IpmCounters {
-  unsigned long long dropped, clipped, small, strip, big;
+  unsigned dropped, clipped, small, strip, big;
 };
 
 // A triangle shared out to the whole warp: frame pixel and frame coordinates.
@@ -294,7 +294,7 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   if (cx0 == cx1 && cy0 == cy1) {
     // whole triangle inside one pixel
     const long long gx = (long long)ox + cx0, gy = (long long)oy + cy0;
-    if (gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix) run_add(M, ra, gx, gy, MM_FIX_ONE);
+    if (gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix) run_add(M, ra, gy * M.npix + gx, MM_FIX_ONE);
     return TRI_DONE;
   }
   // restrict to the map: frame columns [-ox, npix-1-ox]

@@ -161,13 +161,13 @@ __device__ __forceinline__ Vtx shfl_down_vtx(const Vtx &v, int d) {
 
 // Warp-reduce the per-lane triangle counters into the map's statistics.
 __device__ __forceinline__ void flush_counters(const MapDev &M, IpmCounters &cnt, int lane) {
-  unsigned long long v[5] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big};
+  unsigned v[5] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big};
 #pragma unroll
   for (int k = 0; k < 5; k++) {
     for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);
-    if (lane == 0 && v[k]) atomicAdd(&M.stat[k], v[k]);
+    if (lane == 0 && v[k]) atomicAdd(&M.stat[k], (unsigned long long)v[k]);
   }
-  cnt = IpmCounters{0, 0, 0, 0, 0};
+  cnt = IpmCounters{0u, 0u, 0u, 0u, 0u};
 }
 
 // Persistent warps; each work item is a strip of 31 cell columns by
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
     const bool vvalid = i <= M.col_end;  // vertex columns [col_begin, col_end]
     const int cx = __ldg(&M.col_cell[vvalid ? i : M.col_end]);
     const bool cell_col = (lane < MM_STRIP) && (i < M.col_end);
-    RunAcc ra = {LLONG_MIN, LLONG_MIN, 0ull};
+    RunAcc ra = {-1, 0ull};
     Vtx prev;
     {
       const int leaf = lookup_leaf(M, cx, __ldg(&M.row_cell[jb]));
