@@ -17,6 +17,7 @@ rows, rays/s), the end-to-end rate through the C ABI with host buffers, the
 hot kernel's roofline, and the FP64 oracle on the host cores (cpu_baseline).
 """
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -61,6 +62,10 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (the default is the one the metric is quoted on)")
+    ap.add_argument("--rays-per-pixel", type=float, default=None,
+                    help="override the workload's rays per pixel (smaller profiling cases)")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time the map steps only: no FP64 band, end-to-end or CPU legs")
     return ap.parse_args()
 
 
@@ -197,6 +202,8 @@ def run_native(args):
     mm.lib()
 
     wl = synthetic.workload(args.workload)
+    if args.rays_per_pixel:
+        wl = dataclasses.replace(wl, rays_per_pixel=args.rays_per_pixel)
     m, pos = wl.stars()
     args_map = (wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, wl.npix, wl.rays_per_pixel)
     stream = torch.cuda.Stream(device=dev)
@@ -244,38 +251,47 @@ def run_native(args):
     ms_per_step = tot_ms / args.steps
     value = world * rays / (ms_per_step * 1e-3)
 
-    # plain FP64 direct sum on the same GPU: a band of rows sized to ~1 s
-    n0 = st["params"]["n"][0]
-    pairs_per_s = 4e10
-    band = int(max(2, min(st["params"]["n"][1] - 1, pairs_per_s / (n0 * len(m)))))
-    r0 = (st["params"]["n"][1] - 1) // 2 - band // 2
-    hp = mm.create(*args_map, mode=mm.MM_PLAIN_FP64, time_stages=True, row_begin=r0,
-                   row_end=r0 + band)
-    mm.run(hp, stream.cuda_stream)  # warm-up
-    stream.synchronize()
-    mm.run(hp, stream.cuda_stream)
-    sp = mm.get_stats(hp)
-    mm.destroy(hp)
-    plain_rays_s = sp["rays"] / (sp["ms_total"] * 1e-3)
+    fp64_plain, e2e = None, None
+    if not args.kernel_only:
+        # plain FP64 direct sum on the same GPU: a band of rows sized to ~1 s
+        n0 = st["params"]["n"][0]
+        pairs_per_s = 4e10
+        band = int(max(2, min(st["params"]["n"][1] - 1, pairs_per_s / (n0 * len(m)))))
+        r0 = (st["params"]["n"][1] - 1) // 2 - band // 2
+        hp = mm.create(*args_map, mode=mm.MM_PLAIN_FP64, time_stages=True, row_begin=r0,
+                       row_end=r0 + band)
+        mm.run(hp, stream.cuda_stream)  # warm-up
+        stream.synchronize()
+        mm.run(hp, stream.cuda_stream)
+        sp = mm.get_stats(hp)
+        mm.destroy(hp)
+        plain_rays_s = sp["rays"] / (sp["ms_total"] * 1e-3)
 
-    # end to end through the C ABI with host buffers: create (stars H2D),
-    # run, map D2H, destroy
-    m_pin = torch.from_numpy(np.ascontiguousarray(m)).pin_memory()
-    pos_pin = torch.from_numpy(np.ascontiguousarray(pos)).pin_memory()
-    out_pin = torch.empty((wl.npix, wl.npix), dtype=torch.float32).pin_memory()
-    e2e_times = []
-    for k in range(2 + max(1, min(args.steps, 3))):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        he = mm.create(wl.kappa, wl.gamma, wl.s, m_pin.numpy(), pos_pin.numpy(), wl.half_length,
-                       wl.npix, wl.rays_per_pixel, fmm_order=wl.fmm_order)
-        mm.run(he, stream.cuda_stream)
-        mm.get_map(he, out_pin.numpy())
-        mm.destroy(he)
-        t1 = time.perf_counter()
-        if k >= 2:
-            e2e_times.append(t1 - t0)
-    e2e_value = world * rays / float(np.mean(e2e_times))
+        # end to end through the C ABI with host buffers: create (stars H2D),
+        # run, map D2H, destroy
+        m_pin = torch.from_numpy(np.ascontiguousarray(m)).pin_memory()
+        pos_pin = torch.from_numpy(np.ascontiguousarray(pos)).pin_memory()
+        out_pin = torch.empty((wl.npix, wl.npix), dtype=torch.float32).pin_memory()
+        e2e_times = []
+        for k in range(2 + max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            he = mm.create(wl.kappa, wl.gamma, wl.s, m_pin.numpy(), pos_pin.numpy(), wl.half_length,
+                           wl.npix, wl.rays_per_pixel, fmm_order=wl.fmm_order)
+            mm.run(he, stream.cuda_stream)
+            mm.get_map(he, out_pin.numpy())
+            mm.destroy(he)
+            t1 = time.perf_counter()
+            if k >= 2:
+                e2e_times.append(t1 - t0)
+        e2e_value = world * rays / float(np.mean(e2e_times))
+        fp64_plain = {"value": plain_rays_s, "unit": UNIT, "rays": sp["rays"],
+                      "sample": "%d cell rows, full width, same grid" % band,
+                      "speedup_fmm_fp32": value / world / plain_rays_s}
+        e2e = {"value": e2e_value, "unit": UNIT,
+               "h2d_bytes_per_step": int(m.nbytes + pos.nbytes),
+               "d2h_bytes_per_step": int(wl.npix * wl.npix * 4),
+               "includes": "mm_create (stars H2D, plan) + mm_run + mm_get_map (D2H) + mm_destroy"}
 
     # roofline of the hot kernel (FP32 ALU bound)
     p = st["fmm_order"]
@@ -299,7 +315,7 @@ def run_native(args):
         return 0
 
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not (args.no_cpu_baseline or args.kernel_only) and world == 1:
         v, info = oracle_rays_per_s(wl, m, pos, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                "sample": info["sample"]}
@@ -317,16 +333,11 @@ def run_native(args):
         "maps_per_s": world / (ms_per_step * 1e-3),
         "stages_ms": {k: st[k] for k in ("ms_tree", "ms_expansions", "ms_shoot", "ms_normalize",
                                          "ms_total")},
-        "fp64_plain": {"value": plain_rays_s, "unit": UNIT, "rays": sp["rays"],
-                       "sample": "%d cell rows, full width, same grid" % band,
-                       "speedup_fmm_fp32": value / world / plain_rays_s},
+        "fp64_plain": fp64_plain,
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": int(m.nbytes + pos.nbytes),
-                "d2h_bytes_per_step": int(wl.npix * wl.npix * 4),
-                "includes": "mm_create (stars H2D, plan) + mm_run + mm_get_map (D2H) + mm_destroy"},
-        "gpu_launches": st.get("kernel_launches"),
+        "e2e": e2e,
+        "gpu_launches": st["kernel_launches"] * args.steps,
         "clocks": clocks,
         "map_mean": float(mu.mean()),
     }

@@ -113,7 +113,8 @@ typedef struct {
   int64_t cells;            /* grid cells mapped by mm_run */
   int64_t triangles_dropped;/* zero-area or non-finite triangles (last run) */
   int64_t triangles_clipped;/* triangles spanning more than one pixel of the map */
-  int64_t triangles_quad;   /*   of which within a 2 x 2 pixel box */
+  int64_t triangles_line;   /*   of which two pixels split by one grid line */
+  int64_t triangles_quad;   /*   of which 2 x 2 pixels (both grid lines crossed) */
   int64_t triangles_box;    /*   of which with a box of at most 64 map pixels */
   int64_t triangles_rows;   /*   of which larger (pixel rows shared by a warp) */
   int64_t kernel_launches;  /* library kernels launched by the last run (CUB's

@@ -69,7 +69,8 @@ class Stats(ctypes.Structure):
                 ("min_leaf_half_length", ctypes.c_double),
                 ("mean_near_stars", ctypes.c_double), ("rays", ctypes.c_int64),
                 ("cells", ctypes.c_int64), ("triangles_dropped", ctypes.c_int64),
-                ("triangles_clipped", ctypes.c_int64), ("triangles_quad", ctypes.c_int64),
+                ("triangles_clipped", ctypes.c_int64), ("triangles_line", ctypes.c_int64),
+                ("triangles_quad", ctypes.c_int64),
                 ("triangles_box", ctypes.c_int64), ("triangles_rows", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ms_tree", ctypes.c_double),
                 ("ms_expansions", ctypes.c_double), ("ms_shoot", ctypes.c_double),

@@ -999,6 +999,7 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
     out->triangles_quad = (int64_t)st[2];
     out->triangles_box = (int64_t)st[3];
     out->triangles_rows = (int64_t)st[4];
+    out->triangles_line = (int64_t)st[5];
   }
   out->kernel_launches = h->launches;
   if (h->ev_recorded) {

@@ -121,14 +121,13 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
   extern __shared__ __align__(16) unsigned char s_dyn[];
   WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
   WarpQueue wq = {ws->quad, 0};
-  JobQueue jp = {ws->pix, 0};
-  JobQueue jr = {ws->rows, 0};
+  JobQueue jq = {ws->big, 0};
   const MapDev &M = maps[0];
   const int64_t strips = (n0 - 1 + MM_STRIP - 1) / MM_STRIP;
   const int64_t rows = row_hi - row_lo;  // cell rows
   const int64_t rpi = M.rows_per_item;
   const int64_t total = strips * ((rows + rpi - 1) / rpi);
-  IpmCounters cnt = {0, 0, 0, 0, 0};
+  IpmCounters cnt = {0, 0, 0, 0, 0, 0};
   while (true) {
     unsigned long long w = 0;
     if (lane == 0) w = atomicAdd(work_counter, 1ull);
@@ -162,19 +161,17 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
                                                  tri ? cur : cur_r, ra, cnt, se, job)
                                   : TRI_DONE;
         wq_push(M, wq, code == TRI_SMALL, se, lane);
-        jq_push<false>(M, jp, code == TRI_PIX, job, lane);
-        jq_push<true>(M, jr, code == TRI_ROWS, job, lane);
+        jq_push(M, jq, code == TRI_BIG, job, lane);
       }
       prev = cur;
     }
     run_flush(M, ra);
     wq_drain(M, wq, lane);
-    jq_drain<false>(M, jp, lane);
-    jq_drain<true>(M, jr, lane);
+    jq_drain(M, jq, lane);
   }
-  unsigned v[5] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big};
+  unsigned v[MM_N_COUNTERS] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big, cnt.line};
 #pragma unroll
-  for (int k = 0; k < 5; k++) {
+  for (int k = 0; k < MM_N_COUNTERS; k++) {
     for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);
     if (lane == 0 && v[k]) atomicAdd(&M.stat[k], (unsigned long long)v[k]);
   }

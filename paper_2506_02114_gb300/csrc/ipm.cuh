@@ -20,24 +20,28 @@
 // With the box translated to [0, 1]^2 every term is O(1): no cancellation,
 // no polygon arrays, everything in registers.  The same identity with a
 // quadrant (x < X, y < Y) gives the three areas that split a triangle
-// covering a 2 x 2 pixel box.  This computes exactly the areas that the
-// column-then-row Sutherland-Hodgman clipping of Fig. 3 produces.
+// covering a 2 x 2 pixel box; for a pixel of a larger triangle the shoelace
+// sum is taken edge by edge as the integral of the clamped x over the
+// clamped y.  These are exactly the areas that the column-then-row
+// Sutherland-Hodgman clipping of Fig. 3 produces.
 //
 // Paths:
 //   * the triangle lies inside one pixel (the common case at ~100 rays per
 //     pixel): that pixel gains exactly 2^32;
-//   * it spans at most 2 x 2 pixels: queued per warp in shared memory and
+//   * it spans two pixels split by one grid line: the vertex alone on its
+//     side cuts off a similar triangle whose area fraction is a product of
+//     two edge parameters, finished here;
+//   * it spans 2 x 2 pixels: queued per warp in shared memory and
 //     apportioned 32 at a time from three quadrant areas by
 //     inclusion-exclusion;
-//   * its box holds at most MM_MED_PIXELS pixels of the map: the pixels of
-//     all such triangles of a warp are dealt out to its lanes, one pixel
-//     (one box area) per lane at a time;
-//   * larger (cells next to a star map to triangles hundreds of pixels
-//     wide): the pixel rows of all such triangles of a warp are dealt out to
-//     its lanes; each row adds the constant 1/|area| to its run of fully
-//     covered pixels through a per-row difference array and computes only
-//     the partially covered ones, so the work is proportional to the
-//     perimeter, not the area.
+//   * larger (cells next to a star map to triangles up to hundreds of
+//     pixels wide; cells along a caustic to long slivers): queued per warp;
+//     the pixel rows of 32 such triangles are dealt out to the lanes, each
+//     row adds the constant 1/|area| to its run of fully covered pixels
+//     through a per-row difference array, and the partially covered pixels
+//     of those rows are then dealt out one per lane and measured with the
+//     edge integrals of edge_band_integral.  Work is proportional to the
+//     perimeter, not the area, and no lane loops on its own.
 #pragma once
 #include <climits>
 
@@ -103,40 +107,6 @@ __device__ __forceinline__ void run_add(const MapDev &M, RunAcc &a, long long id
 // areas
 // ---------------------------------------------------------------------------
 
-// Signed area of T n [0,1]^2 (orientation of T), T = (x_k, y_k) given
-// relative to the box corner.
-__device__ __forceinline__ float unit_box_area(const float *t) {
-  float s = 0.f;
-#pragma unroll
-  for (int e = 0; e < 3; e++) {
-    const float px = t[2 * e], py = t[2 * e + 1];
-    const float qx = t[(2 * e + 2) % 6], qy = t[(2 * e + 3) % 6];
-    const float dx = qx - px, dy = qy - py;
-    const float rx = rcp_approx_f(dx), ry = rcp_approx_f(dy);
-    float a0 = -px * rx, a1 = (1.f - px) * rx, a2 = -py * ry, a3 = (1.f - py) * ry;
-    a0 = fminf(fmaxf(a0, 0.f), 1.f);
-    a1 = fminf(fmaxf(a1, 0.f), 1.f);
-    a2 = fminf(fmaxf(a2, 0.f), 1.f);
-    a3 = fminf(fmaxf(a3, 0.f), 1.f);
-    // sort the four cut parameters
-    const float l0 = fminf(a0, a1), h0 = fmaxf(a0, a1), l1 = fminf(a2, a3), h1 = fmaxf(a2, a3);
-    const float s0 = fminf(l0, l1), s3 = fmaxf(h0, h1);
-    const float m0 = fmaxf(l0, l1), m1 = fminf(h0, h1);
-    const float s1 = fminf(m0, m1), s2 = fmaxf(m0, m1);
-    const float ts[6] = {0.f, s0, s1, s2, s3, 1.f};
-    float cx = fminf(fmaxf(px, 0.f), 1.f), cy = fminf(fmaxf(py, 0.f), 1.f);
-#pragma unroll
-    for (int k = 1; k < 6; k++) {
-      const float nx = fminf(fmaxf(fmaf(ts[k], dx, px), 0.f), 1.f);
-      const float ny = fminf(fmaxf(fmaf(ts[k], dy, py), 0.f), 1.f);
-      s = fmaf(cx, ny, fmaf(-nx, cy, s));
-      cx = nx;
-      cy = ny;
-    }
-  }
-  return 0.5f * s;
-}
-
 // Signed area of T n {x < X, y < Y} for T = (0,0), d1, d2.
 __device__ __forceinline__ float quad_area(float d1x, float d1y, float d2x, float d2y, float X,
                                            float Y) {
@@ -161,13 +131,6 @@ __device__ __forceinline__ float quad_area(float d1x, float d1y, float d2x, floa
     s = fmaf(p2x, p3y, fmaf(-p3x, p2y, s));
   }
   return 0.5f * s;
-}
-
-// Fraction of T (frame coordinates t, 2/signed area inv2) in frame pixel (c, r).
-__device__ __forceinline__ float pixel_fraction(const float *t, int c, int r, float inv2) {
-  const float fc = (float)c, fr = (float)r;
-  const float u[6] = {t[0] - fc, t[1] - fr, t[2] - fc, t[3] - fr, t[4] - fc, t[5] - fr};
-  return unit_box_area(u) * inv2;
 }
 
 // ---------------------------------------------------------------------------
@@ -242,28 +205,31 @@ __device__ __forceinline__ void wq_drain(const MapDev &M, WarpQueue &wq, int lan
 // ---------------------------------------------------------------------------
 
 // Per-lane triangle counters, reduced per warp into MapDev::stat:
-// [0] dropped, [1] multi-pixel (clipped) in the map, [2] within a 2 x 2 box,
-// [3] box of at most MM_MED_PIXELS pixels (pixel jobs), [4] larger (row jobs).
+// [0] dropped, [1] multi-pixel (clipped) in the map, [2] within a 2 x 2 box
+// crossing both grid lines, [3] box of at most MM_MED_PIXELS pixels (pixel
+// jobs), [4] larger (row jobs), [5] two pixels split by one grid line.
+#define MM_N_COUNTERS 6
 struct IpmCounters {
-  unsigned dropped, clipped, small, strip, big;
+  unsigned dropped, clipped, small, strip, big, line;
 };
 
-// A triangle shared out to the whole warp: frame pixel and frame coordinates.
+// A triangle shared out to the whole warp: frame pixel, frame coordinates,
+// 2 / signed area and the inverse slope dx/dy of each edge k -> k + 1
+// (infinite or NaN for a horizontal edge, which is never used).
 struct __align__(16) TriJob {
   int ox, oy;
   float t[6];
-  float inv2;  // 2 / signed area
-  int pad[3];
+  float inv2;
+  float k[3];
 };
 
-enum { TRI_DONE = 0, TRI_SMALL = 1, TRI_PIX = 2, TRI_ROWS = 3 };
+enum { TRI_DONE = 0, TRI_SMALL = 1, TRI_BIG = 2 };
 
-// Apportion one triangle (a, b, c).  One-pixel triangles are finished here;
-// returns TRI_SMALL (se filled) for a triangle within a 2 x 2 pixel box, to be
-// pushed on the warp queue, TRI_PIX (job filled) when its box within the map
-// holds at most MM_MED_PIXELS pixels, which the warp deals out one pixel per
-// lane (warp_pixel_jobs), and TRI_ROWS (job filled) for a larger one, whose
-// pixel rows the warp deals out (warp_row_jobs).
+// Apportion one triangle (a, b, c).  Triangles within one pixel or split by
+// one grid line are finished here; returns TRI_SMALL (se filled) for a
+// triangle covering 2 x 2 pixels, to be pushed on the quad queue, and TRI_BIG
+// (job filled) for a larger one, whose pixel rows and then partially covered
+// pixels the warp deals out to its lanes (warp_tri_jobs).
 __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
                                             const Vtx &b, const Vtx &c, RunAcc &ra,
                                             IpmCounters &cnt, SmallTri &se, TriJob &job) {
@@ -304,6 +270,41 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   const long long rl = cy0 > mrl ? cy0 : mrl, rh = cy1 < mrh ? cy1 : mrh;
   if (cl > ch || rl > rh) return TRI_DONE;  // misses the map
   cnt.clipped++;
+  if ((cx1 - cx0) + (cy1 - cy0) == 1) {
+    // Two pixels split by one grid line u = L (u = x or y).  The vertex alone
+    // on its side cuts off a triangle similar to the corner it spans, of
+    // area fraction d^2 / ((u_a - u_l)(u_b - u_l)) with d = L - u_l (the two
+    // edge parameters at the line, multiplied).  The shares are complements
+    // in fixed point, so the pair sums to exactly one triangle.
+    const int o = cy1 - cy0;  // 0: vertical line, 1: horizontal line
+    const float L = (float)(o ? cy0 : cx0) + 1.f;
+    const float u0 = t[o], u1 = t[2 + o], u2 = t[4 + o];
+    const bool b0 = u0 < L, b1 = u1 < L, b2 = u2 < L;
+    const bool lone_low = (b0 + b1 + b2) == 1;
+    float ul = u2, ua = u0, ub = u1;
+    if (b0 == lone_low) {
+      ul = u0;
+      ua = u1;
+      ub = u2;
+    } else if (b1 == lone_low) {
+      ul = u1;
+      ua = u0;
+      ub = u2;
+    }
+    const float d = L - ul;
+    const unsigned long long vl = frac_to_fixed(d * d * rcp_approx_f((ua - ul) * (ub - ul)));
+    const unsigned long long vlow = lone_low ? vl : MM_FIX_ONE - vl;
+    // the pixel holding vertex a goes through the run accumulator
+    const long long glx = (long long)ox + cx0, gly = (long long)oy + cy0;  // low pixel
+    const long long gax = b0 ? glx : glx + 1 - o, gay = b0 ? gly : gly + o;
+    const long long gbx = b0 ? glx + 1 - o : glx, gby = b0 ? gly + o : gly;
+    const unsigned long long va = b0 ? vlow : MM_FIX_ONE - vlow;
+    if (va && gax >= 0 && gax < M.npix && gay >= 0 && gay < M.npix)
+      run_add(M, ra, gay * M.npix + gax, va);
+    deposit(M, gbx, gby, MM_FIX_ONE - va);
+    cnt.line++;
+    return TRI_DONE;
+  }
   if (cx1 - cx0 <= 1 && cy1 - cy0 <= 1) {
     se.ox = ox;
     se.oy = oy;
@@ -321,240 +322,202 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
 #pragma unroll
   for (int k = 0; k < 6; k++) job.t[k] = t[k];
   job.inv2 = 2.0f / area2;
-  if ((ch - cl + 1) * (rh - rl + 1) <= MM_MED_PIXELS) {
+#pragma unroll
+  for (int e = 0; e < 3; e++)
+    job.k[e] = (t[(2 * e + 2) % 6] - t[2 * e]) / (t[(2 * e + 3) % 6] - t[2 * e + 1]);
+  if ((ch - cl + 1) * (rh - rl + 1) <= MM_MED_PIXELS)
     cnt.strip++;
-    return TRI_PIX;
-  }
-  cnt.big++;
-  return TRI_ROWS;
+  else
+    cnt.big++;
+  return TRI_BIG;
 }
 
 // ---------------------------------------------------------------------------
-// big triangles: the whole warp, lanes over pixel rows
+// larger triangles: the whole warp, lanes over pixel rows, then over the
+// partially covered pixels of those rows
 // ---------------------------------------------------------------------------
 
-// x-interval of the intersection of the horizontal line y = Y with triangle
-// t; returns false when the line misses it.
-__device__ __forceinline__ bool line_span(const float *t, float Y, float &lo, float &hi) {
-  lo = 3.0e38f;
-  hi = -3.0e38f;
-  bool any = false;
+// Integral over y in [0, 1] of clamp(x(y), 0, 1) along the edge P -> Q
+// (pixel-local coordinates, k = dx/dy of the edge); signed by the direction
+// of y.  Summed over T's three edges this is area(T n [0, 1]^2), signed by
+// T's orientation (Green's theorem on the clamped boundary, as above).  The
+// x-average of clamp over [a, b] is formed from sub-interval lengths, so a
+// nearly vertical piece loses no precision.  x on the edge is extrapolated
+// from the nearer endpoint, which halves the error the rounding of k makes
+// on long edges.
+__device__ __forceinline__ float edge_x_at(float y, float px, float py, float qx, float qy,
+                                          float k) {
+  const float d1 = y - py, d2 = y - qy;
+  return fabsf(d1) <= fabsf(d2) ? fmaf(d1, k, px) : fmaf(d2, k, qx);
+}
+
+__device__ __forceinline__ float edge_band_integral(float px, float py, float qx, float qy,
+                                                    float k) {
+  const float ys = fminf(fmaxf(py, 0.f), 1.f), ye = fminf(fmaxf(qy, 0.f), 1.f);
+  const float xs = edge_x_at(ys, px, py, qx, qy, k), xe = edge_x_at(ye, px, py, qx, qy, k);
+  const float a = fminf(xs, xe), b = fmaxf(xs, xe);
+  const float w = fminf(fmaxf(a, 0.f), 1.f), v = fminf(fmaxf(b, 0.f), 1.f);
+  const float in = fmaf(0.5f * (v - w), v + w, fmaxf(b - fmaxf(a, 1.f), 0.f));
+  const float len = b - a;
+  const float avg = len > 0.f ? in * rcp_approx_f(len) : w;
+  return ye != ys ? (ye - ys) * avg : 0.f;
+}
+
+// Share of triangle J in frame pixel (c, r).
+__device__ __forceinline__ float tri_pixel_fraction(const TriJob &J, int c, int r) {
+  const float fc = (float)c, fr = (float)r;
+  const float x0 = J.t[0] - fc, y0 = J.t[1] - fr;
+  const float x1 = J.t[2] - fc, y1 = J.t[3] - fr;
+  const float x2 = J.t[4] - fc, y2 = J.t[5] - fr;
+  const float s = edge_band_integral(x0, y0, x1, y1, J.k[0]) +
+                  edge_band_integral(x1, y1, x2, y2, J.k[1]) +
+                  edge_band_integral(x2, y2, x0, y0, J.k[2]);
+  return s * J.inv2;
+}
+
+// Frame row r of J: the columns [c0, c1] its band meets (widened by a small
+// margin; extra columns get zero area) and the fully covered run [fa, fb]
+// (empty when fa > fb), whose columns have all four corners in T (T convex):
+// fa >= both left ends and fb + 1 <= both right ends of T's chords on the
+// lines y = r and y = r + 1.
+__device__ __forceinline__ void tri_row_extent(const TriJob &J, int r, int &c0, int &c1,
+                                               int &fa, int &fb) {
+  const float y0 = (float)r, y1 = (float)(r + 1);
+  float l0 = 3.0e38f, h0 = -3.0e38f, l1 = 3.0e38f, h1 = -3.0e38f;
+  float bx0 = 3.0e38f, bx1 = -3.0e38f;
 #pragma unroll
   for (int e = 0; e < 3; e++) {
-    const float x0 = t[2 * e], y0 = t[2 * e + 1];
-    const float x1 = t[(2 * e + 2) % 6], y1 = t[(2 * e + 3) % 6];
-    if (y0 == y1) {
-      if (y0 == Y) {
-        lo = fminf(lo, fminf(x0, x1));
-        hi = fmaxf(hi, fmaxf(x0, x1));
-        any = true;
+    const float px = J.t[2 * e], py = J.t[2 * e + 1];
+    const float qy = J.t[(2 * e + 3) % 6];
+    const float lo = fminf(py, qy), hi = fmaxf(py, qy);
+    if (lo < hi) {
+      const float xa = fmaf(y0 - py, J.k[e], px);
+      const float xb = fmaf(y1 - py, J.k[e], px);
+      if (lo <= y0 && y0 <= hi) l0 = fminf(l0, xa), h0 = fmaxf(h0, xa);
+      if (lo <= y1 && y1 <= hi) l1 = fminf(l1, xb), h1 = fmaxf(h1, xb);
+    }
+    if (py >= y0 && py <= y1) bx0 = fminf(bx0, px), bx1 = fmaxf(bx1, px);
+  }
+  bx0 = fminf(bx0, fminf(l0, l1));
+  bx1 = fmaxf(bx1, fmaxf(h0, h1));
+  const float eps = 1e-3f, lim = 1.0e9f;
+  c0 = (int)floorf(fminf(fmaxf(bx0 - eps, -lim), lim));
+  c1 = (int)floorf(fminf(fmaxf(bx1 + eps, -lim), lim));
+  fa = 1;
+  fb = 0;
+  if (h0 >= l0 && h1 >= l1) {
+    fa = (int)ceilf(fminf(fmaxf(fmaxf(l0, l1) + eps, -lim), lim));
+    fb = (int)floorf(fminf(fmaxf(fminf(h0, h1) - eps, -lim), lim)) - 1;
+  }
+}
+
+// Owner lane of task `task`: the first lane whose inclusive count exceeds it.
+__device__ __forceinline__ int scan_owner(int incl, int task) {
+  int lo = 0, hi = 31;
+#pragma unroll
+  for (int it = 0; it < 5; it++) {
+    const int mid = (lo + hi) >> 1;
+    if (__shfl_sync(0xffffffffu, incl, mid) > task)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += u;
+  }
+  return v;
+}
+
+// The nb (<= 32) triangles q[0..nb) (warp shared memory) spanning more than
+// 2 x 2 pixels.  Their pixel rows within the map are dealt out to the lanes,
+// 32 at a time; a row adds 1/|area| to its fully covered run through the
+// row difference array, and the partially covered pixels of those 32 rows
+// are then dealt out one per lane.  Work is proportional to the perimeter,
+// and the lanes stay busy however the rows differ.  Call with all 32 lanes.
+static __device__ __noinline__ void warp_tri_jobs(const MapDev &M, const TriJob *q, int nb,
+                                                  int lane) {
+  int rl = 0, nrows = 0;
+  if (lane < nb) {
+    const TriJob &J = q[lane];
+    const float ymin = fminf(J.t[1], fminf(J.t[3], J.t[5]));
+    const float ymax = fmaxf(J.t[1], fmaxf(J.t[3], J.t[5]));
+    const int r0 = max((int)floorf(fmaxf(ymin, -1.0e9f)), -J.oy);
+    const int r1 = min((int)floorf(fminf(ymax, 1.0e9f)), M.npix - 1 - J.oy);
+    rl = r0;
+    nrows = r1 >= r0 ? r1 - r0 + 1 : 0;
+  }
+  const int incl = warp_incl_scan(nrows, lane);
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  for (int base = 0; base < total; base += 32) {
+    const int task = base + lane;
+    const int k = scan_owner(incl, task);
+    const int r = __shfl_sync(0xffffffffu, rl, k) + task - __shfl_sync(0xffffffffu, incl - nrows, k);
+    int c0 = 0, fa = 1, fb = 0, np = 0;
+    if (task < total) {
+      const TriJob &J = q[k];
+      int c1;
+      tri_row_extent(J, r, c0, c1, fa, fb);
+      c0 = max(c0, -J.ox);
+      c1 = min(c1, M.npix - 1 - J.ox);
+      fa = max(fa, c0);
+      fb = min(fb, c1);
+      if (c0 <= c1) {
+        np = c1 - c0 + 1;
+        if (fa <= fb) {
+          np -= fb - fa + 1;
+          // a fully covered pixel holds 1/|area| of the triangle (< 1 when any does)
+          const unsigned long long full = frac_to_fixed(fabsf(J.inv2));
+          unsigned long long *sp = M.span + (long long)(J.oy + r) * (M.npix + 1);
+          atomicAdd(&sp[J.ox + fa], full);
+          atomicAdd(&sp[J.ox + fb + 1], 0ull - full);
+        }
       }
-    } else if ((y0 <= Y && Y <= y1) || (y1 <= Y && Y <= y0)) {
-      const float x = x0 + (Y - y0) * (x1 - x0) / (y1 - y0);
-      lo = fminf(lo, x);
-      hi = fmaxf(hi, x);
-      any = true;
+    }
+    // the partially covered pixels of these 32 rows
+    const int pincl = warp_incl_scan(np, lane);
+    const int ptotal = __shfl_sync(0xffffffffu, pincl, 31);
+    for (int pbase = 0; pbase < ptotal; pbase += 32) {
+      const int ptask = pbase + lane;
+      const int j = scan_owner(pincl, ptask);
+      const int jk = __shfl_sync(0xffffffffu, k, j);
+      const int jr = __shfl_sync(0xffffffffu, r, j);
+      const int jc0 = __shfl_sync(0xffffffffu, c0, j);
+      const int jfa = __shfl_sync(0xffffffffu, fa, j);
+      const int jfb = __shfl_sync(0xffffffffu, fb, j);
+      const int jst = __shfl_sync(0xffffffffu, pincl - np, j);
+      if (ptask < ptotal) {
+        int c = jc0 + (ptask - jst);
+        if (jfa <= jfb && c >= jfa) c += jfb - jfa + 1;
+        const TriJob &J = q[jk];
+        deposit(M, (long long)J.ox + c, (long long)J.oy + jr,
+                frac_to_fixed(tri_pixel_fraction(J, c, jr)));
+      }
     }
   }
-  return any;
+  __syncwarp();
 }
 
-// Pixel row r (frame coordinates) of a big triangle.  The fully covered
-// columns are those whose four corners lie in T (T convex):
-// [max(l0, l1), min(r0, r1)] with [l0, r0] and [l1, r1] the spans of T on
-// the lines y = r and y = r + 1; they receive 2^32/|area| through the row
-// difference array.  The row's x-extent is the union of those spans and of
-// the vertices inside the band; the remaining columns are computed exactly.
-__device__ __forceinline__ void span_row(const MapDev &M, const TriJob &J,
-                                         long long r, long long cl, long long ch,
-                                         unsigned long long full) {
-  const float y0 = (float)r, y1 = (float)(r + 1);
-  float l0, r0, l1, r1;
-  const bool s0 = line_span(J.t, y0, l0, r0);
-  const bool s1 = line_span(J.t, y1, l1, r1);
-  float bx0 = 3.0e38f, bx1 = -3.0e38f;
-  if (s0) bx0 = fminf(bx0, l0), bx1 = fmaxf(bx1, r0);
-  if (s1) bx0 = fminf(bx0, l1), bx1 = fmaxf(bx1, r1);
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    const float vy = J.t[2 * k + 1];
-    if (vy >= y0 && vy <= y1) bx0 = fminf(bx0, J.t[2 * k]), bx1 = fmaxf(bx1, J.t[2 * k]);
-  }
-  if (!(bx0 <= bx1)) return;
-  long long c0 = (int)floorf(fmaxf(bx0, -1.0e9f));
-  long long c1 = (int)floorf(fminf(bx1, 1.0e9f));
-  if (c0 < cl) c0 = cl;
-  if (c1 > ch) c1 = ch;
-  if (c0 > c1) return;
-  long long fa = 1, fb = 0;  // fully covered columns [fa, fb]
-  if (s0 && s1) {
-    const float eps = 1e-3f;
-    fa = (int)ceilf(fminf(fmaxf(l0, l1) + eps, 1.0e9f));
-    fb = (long long)(int)floorf(fmaxf(fminf(r0, r1) - eps, -1.0e9f)) - 1;
-    if (fa < c0) fa = c0;
-    if (fb > c1) fb = c1;
-  }
-  const long long row = (long long)J.oy + r;
-  for (long long c = c0; c <= c1; c++) {
-    if (fa <= fb && c == fa) {
-      c = fb;  // skip the fully covered run
-      continue;
-    }
-    deposit(M, (long long)J.ox + c, row,
-            frac_to_fixed(pixel_fraction(J.t, (int)c, (int)r, J.inv2)));
-  }
-  if (fa <= fb) {
-    unsigned long long *sp = M.span + row * (M.npix + 1);
-    atomicAdd(&sp[J.ox + fa], full);
-    atomicAdd(&sp[J.ox + fb + 1], 0ull - full);
-  }
-}
-
-// Lanes whose `have` is set hold a triangle spanning more than a 2 x 2 box;
-// the pixel rows of all of them (within the map) are dealt out to the 32
-// lanes, one row per lane at a time.  A lane finds the triangle owning its
-// row by binary search over the warp's inclusive scan of row counts and
-// takes that triangle from its owner by shuffles.  Call with all 32 lanes.
-static __device__ __noinline__ void warp_row_jobs(const MapDev &M, bool have, const TriJob &job,
-                                           int lane) {
-  if (!__any_sync(0xffffffffu, have)) return;
-  int rl = 0, nrows = 0, cl = 0, ch = -1;
-  if (have) {
-    const float ymin = fminf(job.t[1], fminf(job.t[3], job.t[5]));
-    const float ymax = fmaxf(job.t[1], fmaxf(job.t[3], job.t[5]));
-    const float xmin = fminf(job.t[0], fminf(job.t[2], job.t[4]));
-    const float xmax = fmaxf(job.t[0], fmaxf(job.t[2], job.t[4]));
-    long long r0 = (int)floorf(fmaxf(ymin, -1.0e9f));
-    long long r1 = (int)floorf(fminf(ymax, 1.0e9f));
-    long long c0 = (int)floorf(fmaxf(xmin, -1.0e9f));
-    long long c1 = (int)floorf(fminf(xmax, 1.0e9f));
-    if (r0 < -(long long)job.oy) r0 = -(long long)job.oy;
-    if (r1 > (long long)M.npix - 1 - job.oy) r1 = (long long)M.npix - 1 - job.oy;
-    if (c0 < -(long long)job.ox) c0 = -(long long)job.ox;
-    if (c1 > (long long)M.npix - 1 - job.ox) c1 = (long long)M.npix - 1 - job.ox;
-    rl = (int)r0;
-    cl = (int)c0;
-    ch = (int)c1;
-    nrows = r1 >= r0 ? (int)(r1 - r0 + 1) : 0;
-  }
-  int incl = nrows;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += v;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  for (int base = 0; base < total; base += 32) {
-    const int task = base + lane;
-    // owner: the first lane whose inclusive count exceeds task
-    int lo = 0, hi = 31;
-#pragma unroll
-    for (int it = 0; it < 5; it++) {
-      const int mid = (lo + hi) >> 1;
-      const int v = __shfl_sync(0xffffffffu, incl, mid);
-      if (v > task)
-        hi = mid;
-      else
-        lo = mid + 1;
-    }
-    const int k = lo;
-    TriJob J;
-    J.ox = __shfl_sync(0xffffffffu, job.ox, k);
-    J.oy = __shfl_sync(0xffffffffu, job.oy, k);
-#pragma unroll
-    for (int q = 0; q < 6; q++) J.t[q] = __shfl_sync(0xffffffffu, job.t[q], k);
-    J.inv2 = __shfl_sync(0xffffffffu, job.inv2, k);
-    const int krl = __shfl_sync(0xffffffffu, rl, k);
-    const int kcl = __shfl_sync(0xffffffffu, cl, k);
-    const int kch = __shfl_sync(0xffffffffu, ch, k);
-    const int kn = __shfl_sync(0xffffffffu, nrows, k);
-    const int kincl = __shfl_sync(0xffffffffu, incl, k);
-    if (task < total) {
-      // a fully covered pixel holds 1/|area| of the triangle (< 1 when any does)
-      const unsigned long long full = frac_to_fixed(fabsf(J.inv2));
-      span_row(M, J, krl + (task - (kincl - kn)), kcl, kch, full);
-    }
-  }
-}
-
-// Lanes whose `have` is set hold a triangle whose box (within the map) holds
-// at most MM_MED_PIXELS pixels; all those pixels are dealt out to the 32
-// lanes, one per lane at a time, and each lane adds its pixel's share.
-static __device__ __noinline__ void warp_pixel_jobs(const MapDev &M, bool have, const TriJob &job,
-                                             int lane) {
-  if (!__any_sync(0xffffffffu, have)) return;
-  int c0 = 0, r0 = 0, w = 1, npx = 0;
-  if (have) {
-    const float xmin = fminf(job.t[0], fminf(job.t[2], job.t[4]));
-    const float xmax = fmaxf(job.t[0], fmaxf(job.t[2], job.t[4]));
-    const float ymin = fminf(job.t[1], fminf(job.t[3], job.t[5]));
-    const float ymax = fmaxf(job.t[1], fmaxf(job.t[3], job.t[5]));
-    int cl = (int)floorf(xmin), ch = (int)floorf(xmax);
-    int rl = (int)floorf(ymin), rh = (int)floorf(ymax);
-    cl = max(cl, -job.ox);
-    ch = min(ch, M.npix - 1 - job.ox);
-    rl = max(rl, -job.oy);
-    rh = min(rh, M.npix - 1 - job.oy);
-    c0 = cl;
-    r0 = rl;
-    w = ch - cl + 1;
-    npx = (ch >= cl && rh >= rl) ? w * (rh - rl + 1) : 0;
-  }
-  int incl = npx;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += v;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  for (int base = 0; base < total; base += 32) {
-    const int task = base + lane;
-    int lo = 0, hi = 31;
-#pragma unroll
-    for (int it = 0; it < 5; it++) {
-      const int mid = (lo + hi) >> 1;
-      if (__shfl_sync(0xffffffffu, incl, mid) > task)
-        hi = mid;
-      else
-        lo = mid + 1;
-    }
-    const int k = lo;
-    float t[6];
-#pragma unroll
-    for (int q = 0; q < 6; q++) t[q] = __shfl_sync(0xffffffffu, job.t[q], k);
-    const int kox = __shfl_sync(0xffffffffu, job.ox, k);
-    const int koy = __shfl_sync(0xffffffffu, job.oy, k);
-    const float kinv = __shfl_sync(0xffffffffu, job.inv2, k);
-    const int kc0 = __shfl_sync(0xffffffffu, c0, k);
-    const int kr0 = __shfl_sync(0xffffffffu, r0, k);
-    const int kw = __shfl_sync(0xffffffffu, w, k);
-    const int kstart = __shfl_sync(0xffffffffu, incl - npx, k);
-    if (task < total) {
-      const int q = task - kstart;
-      const int c = kc0 + q % kw, r = kr0 + q / kw;
-      deposit(M, (long long)kox + c, (long long)koy + r,
-              frac_to_fixed(pixel_fraction(t, c, r, kinv)));
-    }
-  }
-}
-
-// Per-warp queue of triangles for the pixel (PIX) or row (ROWS) jobs, in
-// shared memory (capacity 64 >= 31 + 31 + 2).  A full batch of 32 is shared
-// out at once, so the lanes stay busy and the dealing overhead is amortised.
+// Per-warp queue of larger triangles in shared memory (capacity 64 >=
+// 31 + 31 + 2).  A full batch of 32 is shared out at once, so the lanes stay
+// busy and the dealing overhead is amortised.
 struct JobQueue {
   TriJob *q;
   int n;
 };
 
-// Shared memory of one warp: the three queues.
+// Shared memory of one warp: the two queues.
 struct WarpSmem {
   SmallTri quad[64];
-  TriJob pix[64];
-  TriJob rows[64];
+  TriJob big[64];
 };
 #define MM_SHOOT_SMEM_BYTES (8 * sizeof(WarpSmem))  // 8 warps per block
 
-template <bool ROWS>
 __device__ __forceinline__ void jq_push(const MapDev &M, JobQueue &jq, bool want,
                                         const TriJob &job, int lane) {
   const unsigned m = __ballot_sync(0xffffffffu, want);
@@ -564,29 +527,14 @@ __device__ __forceinline__ void jq_push(const MapDev &M, JobQueue &jq, bool want
   jq.n += __popc(m);
   __syncwarp();
   while (jq.n >= 32) {
-    const TriJob t = jq.q[jq.n - 32 + lane];
-    __syncwarp();
     jq.n -= 32;
-    if (ROWS)
-      warp_row_jobs(M, true, t, lane);
-    else
-      warp_pixel_jobs(M, true, t, lane);
+    warp_tri_jobs(M, jq.q + jq.n, 32, lane);
   }
 }
 
-template <bool ROWS>
 __device__ __forceinline__ void jq_drain(const MapDev &M, JobQueue &jq, int lane) {
-  if (jq.n > 0) {
-    const bool have = lane < jq.n;
-    TriJob t;
-    if (have) t = jq.q[lane];
-    __syncwarp();
-    jq.n = 0;
-    if (ROWS)
-      warp_row_jobs(M, have, t, lane);
-    else
-      warp_pixel_jobs(M, have, t, lane);
-  }
+  if (jq.n > 0) warp_tri_jobs(M, jq.q, jq.n, lane);
+  jq.n = 0;
   __syncwarp();
 }
 

@@ -12,8 +12,8 @@
 #define MM_DMAX 21            // deepest quadtree level
 #define MM_PMAX 64            // largest expansion order accepted by the ABI
 #define MM_STRIP 31           // cell columns per warp work item (32 vertex columns)
-#define MM_MED_PIXELS 64      // bounding box (pixels) up to which a triangle is
-                              // apportioned from quadrant areas by one lane
+#define MM_MED_PIXELS 64      // bounding box (map pixels) up to which a larger
+                              // triangle is counted as medium in the statistics
 
 namespace mm {
 

@@ -161,13 +161,13 @@ __device__ __forceinline__ Vtx shfl_down_vtx(const Vtx &v, int d) {
 
 // Warp-reduce the per-lane triangle counters into the map's statistics.
 __device__ __forceinline__ void flush_counters(const MapDev &M, IpmCounters &cnt, int lane) {
-  unsigned v[5] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big};
+  unsigned v[MM_N_COUNTERS] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big, cnt.line};
 #pragma unroll
-  for (int k = 0; k < 5; k++) {
+  for (int k = 0; k < MM_N_COUNTERS; k++) {
     for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);
     if (lane == 0 && v[k]) atomicAdd(&M.stat[k], (unsigned long long)v[k]);
   }
-  cnt = IpmCounters{0u, 0u, 0u, 0u, 0u};
+  cnt = IpmCounters{0u, 0u, 0u, 0u, 0u, 0u};
 }
 
 // Persistent warps; each work item is a strip of 31 cell columns by
@@ -189,9 +189,8 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
   extern __shared__ __align__(16) unsigned char s_dyn[];
   WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
   WarpQueue wq = {ws->quad, 0};
-  JobQueue jp = {ws->pix, 0};
-  JobQueue jr = {ws->rows, 0};
-  IpmCounters cnt = {0, 0, 0, 0, 0};
+  JobQueue jq = {ws->big, 0};
+  IpmCounters cnt = {0, 0, 0, 0, 0, 0};
   int last_map = -1;
   while (true) {
     unsigned long long w = 0;
@@ -246,15 +245,13 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
                                                  tri ? cur : cur_r, ra, cnt, se, job)
                                   : TRI_DONE;
         wq_push(M, wq, code == TRI_SMALL, se, lane);
-        jq_push<false>(M, jp, code == TRI_PIX, job, lane);
-        jq_push<true>(M, jr, code == TRI_ROWS, job, lane);
+        jq_push(M, jq, code == TRI_BIG, job, lane);
       }
       prev = cur;
     }
     run_flush(M, ra);
     wq_drain(M, wq, lane);
-    jq_drain<false>(M, jp, lane);
-    jq_drain<true>(M, jr, lane);
+    jq_drain(M, jq, lane);
   }
   if (last_map >= 0) flush_counters(maps[last_map], cnt, lane);
 }
