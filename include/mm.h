@@ -68,8 +68,16 @@ typedef struct {
   double center_y[2];       /* map centre in the source plane (Sec. 2.3) */
   int64_t row_begin;        /* shoot only cell rows [row_begin, row_end) of the */
   int64_t row_end;          /*   ray grid; both 0 -> every row */
-  int32_t rows_per_item;    /* rows of cells per warp work item, 1..4096; 0 -> 64 */
-  int32_t reserved;
+  int32_t rows_per_item;    /* rows of cells per warp work item, 1..4096; 0 ->
+                               the largest of 256, 128, ..., 16 that leaves every
+                               resident warp >= 16 items */
+  int32_t sub_levels;       /* FMM mode: each leaf's local expansion is re-centred
+                               exactly on its 4^s sub-cells (s levels below the
+                               leaf) and evaluated to the fewest terms whose
+                               truncation bound matches order p at the leaf
+                               centre (App. C error model).  -1: none; 0: the
+                               default (2); 1 or 2: s.  Capped so that leaves
+                               plus sub-cells stay within 21 tree levels. */
   int64_t col_begin;        /* shoot only cell columns [col_begin, col_end) of */
   int64_t col_end;          /*   the ray grid; both 0 -> every column */
 } mm_options;
@@ -101,6 +109,8 @@ typedef struct {
   int32_t fmm_order;        /* expansion order p actually used */
   int32_t leaf_size;        /* maximum stars used directly (App. C.1), default 32 */
   int32_t depth;            /* deepest tree level */
+  int32_t eval_order;       /* terms of the re-centred expansion evaluated per ray */
+  int32_t sub_levels;       /* sub-cell levels s actually used */
   int64_t n_stars;
   int64_t nodes;            /* tree nodes over all levels */
   int64_t leaves;           /* leaves over all levels */

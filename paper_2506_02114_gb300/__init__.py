@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("img_half", ctypes.c_double * 2), ("ray_grid", ctypes.c_int64 * 2),
                 ("flux_fraction_f", ctypes.c_double), ("center_y", ctypes.c_double * 2),
                 ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
-                ("rows_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rows_per_item", ctypes.c_int32), ("sub_levels", ctypes.c_int32),
                 ("col_begin", ctypes.c_int64), ("col_end", ctypes.c_int64)]
 
 
@@ -63,6 +63,7 @@ class Params(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("params", Params), ("mode", ctypes.c_int32), ("fmm_order", ctypes.c_int32),
                 ("leaf_size", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("eval_order", ctypes.c_int32), ("sub_levels", ctypes.c_int32),
                 ("n_stars", ctypes.c_int64), ("nodes", ctypes.c_int64),
                 ("leaves", ctypes.c_int64), ("active_leaves", ctypes.c_int64),
                 ("root_half_length", ctypes.c_double),
@@ -161,7 +162,7 @@ def _ptr(a):
 
 def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=None,
                  flux_fraction_f=0.0, center_y=(0.0, 0.0), row_begin=0, row_end=0,
-                 rows_per_item=0, col_begin=0, col_end=0):
+                 rows_per_item=0, col_begin=0, col_end=0, sub_levels=0):
     o = Options()
     o.mode = int(mode)
     o.time_stages = 1 if time_stages else 0
@@ -173,6 +174,7 @@ def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=No
     o.center_y[0], o.center_y[1] = float(center_y[0]), float(center_y[1])
     o.row_begin, o.row_end = int(row_begin), int(row_end)
     o.rows_per_item = int(rows_per_item)
+    o.sub_levels = int(sub_levels)
     o.col_begin, o.col_end = int(col_begin), int(col_end)
     return o
 

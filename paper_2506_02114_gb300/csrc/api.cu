@@ -120,6 +120,7 @@ struct mm_map {
   mm_options opt{};
   int mode = MM_FMM_FP32;
   int p = 0, leaf_size = 32;
+  int sub = 0, p_eval = 0;         // sub-cell levels; terms evaluated per ray
   int64_t N = 0;
   double R0 = 1.0;
   int64_t row_lo = 0, row_hi = 0;  // cell rows [row_lo, row_hi)
@@ -375,6 +376,20 @@ static mm_status run_tree(mm_map *h, cudaStream_t st, bool plan) {
   return MM_OK;
 }
 
+// Terms of a sub-cell's re-centred local expansion evaluated per ray.  The
+// far-field stars of a leaf of half-length L lie outside its 3 x 3 block
+// (L-inf distance >= 3L from the centre), so truncating the expansion about
+// the leaf centre at order p errs by ~ (sqrt(2) L / 3L)^p at a corner.  About
+// the centre of a sub-cell of half-length L/2^s the ratio is
+// sqrt(2) 2^-s / (2 + 2^-s); keep the fewest terms that do as well.
+static int eval_terms(int p, int s) {
+  if (s <= 0 || p <= 2) return p;
+  const double r0 = std::sqrt(2.0) / 3.0;
+  const double q = std::ldexp(1.0, -s), rs = std::sqrt(2.0) * q / (2.0 + q);
+  const int pe = (int)std::ceil(p * std::log(r0) / std::log(rs) - 1e-9);
+  return std::max(2, std::min(p, pe));
+}
+
 // Active region, expansions, leaf records and the lookup grid.
 static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
   const mm_params &P = h->P;
@@ -419,12 +434,17 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
     for (int32_t id : al) ml = std::max(ml, (int)lv[id]);
     h->max_leaf_level = ml;
     h->min_leaf_L = h->R0 / (double)(1ll << ml);
+    // sub-cells: finest-level cell indices must still resolve them
+    h->sub = h->opt.sub_levels < 0 ? 0 : (h->opt.sub_levels == 0 ? MM_SUB_DEFAULT
+                                                                  : h->opt.sub_levels);
+    h->sub = std::max(0, std::min(h->sub, MM_DMAX - ml));
     // App. C.3: p > log2(<m^2>/<m> / (L |eps|)), eps = 1/10 of the pixel side
     if (h->p == 0) {
       double arg = (P.m2_over_m > 0.0) ? P.m2_over_m / (h->min_leaf_L * 0.1 * P.delta) : 1.0;
       int p = (int)std::floor(std::log2(std::max(arg, 1.0))) + 1;
       h->p = std::min(MM_PMAX, std::max(2, p));
     }
+    h->p_eval = eval_terms(h->p, h->sub);
     std::vector<double2> MMh, MLh, LLh;
     build_operator_tables(h->p, MMh, MLh, LLh);
     CK(h->MMop.ensure(MMh.size()));
@@ -469,13 +489,16 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
     int32_t b = read_scalar(h->near_cnt.p + (h->n_active - 1), st, e);
     CK(e);
     h->n_near = (int64_t)a + b;
-    CK(h->leaf.ensure(h->n_active));
+    const int64_t n_rec = h->n_active << (2 * h->sub);
+    CK(h->leaf.ensure(n_rec));
     CK(h->near_pos.ensure(h->n_near));
     CK(h->near_m.ensure(h->n_near));
-    CK(h->coef.ensure((size_t)h->n_active * std::max(1, p - 1)));
+    CK(h->coef.ensure((size_t)n_rec * coef_stride(h->p_eval)));
   }
   FmmConst C;
   C.p = p;
+  C.p_eval = h->p_eval;
+  C.sub = h->sub;
   C.kappa = P.kappa;
   C.gamma = P.gamma;
   C.kappa_star = P.kappa_star;
@@ -486,8 +509,9 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
   C.lox = P.center_y[0] - P.half_length;
   C.loy = P.center_y[1] - P.half_length;
   C.delta = P.delta;
-  LCH(launch_leaf_finalize(T, C, h->n_active, h->active_list.p, h->near_off.p, h->loc.p,
-                          h->leaf.p, h->near_pos.p, h->near_m.p, h->coef.p, h->err.p, st));
+  LCH(launch_leaf_finalize(T, C, h->n_active, h->active_list.p, h->near_off.p, h->near_cnt.p,
+                          h->loc.p, h->leaf.p, h->near_pos.p, h->near_m.p, h->coef.p,
+                          h->err.p, st));
 
   if (plan) {
     // lookup grid over the active cell rectangle, as deep as 4M entries allow
@@ -500,7 +524,8 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
     CK(e);
     int CY1 = read_scalar(h->row_cell.p + h->row_hi, st, e);
     CK(e);
-    int gl = h->max_leaf_level;
+    // (deep enough to resolve sub-cells where entries allow)
+    int gl = std::min(MM_DMAX, h->max_leaf_level + h->sub);
     for (; gl > 0; gl--) {
       const int sh = MM_DMAX - gl;
       const int64_t w = (int64_t)(CX1 >> sh) - (CX0 >> sh) + 1;
@@ -515,9 +540,17 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
     h->gh = (CY1 >> h->gshift) - h->gy0 + 1;
     CK(h->grid.ensure((size_t)h->gw * h->gh));
   }
-  LCH(launch_lookup_grid(T, h->node_active.p, h->glevel, h->gx0, h->gy0, h->gw, h->gh,
+  LCH(launch_lookup_grid(T, h->node_active.p, h->glevel, h->sub, h->gx0, h->gy0, h->gw, h->gh,
                         h->grid.p, st));
   return MM_OK;
+}
+
+static int shoot_grid() {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  per_sm = MM_SHOOT_MINB;  // resident 256-thread blocks per SM
+  return std::max(1, sms * per_sm);
 }
 
 static void fill_mapdev(mm_map *h) {
@@ -531,6 +564,14 @@ static void fill_mapdev(mm_map *h) {
   M.col_begin = h->col_lo;
   M.col_end = h->col_hi;
   M.strips = (int32_t)((h->col_hi - h->col_lo + MM_STRIP - 1) / MM_STRIP);
+  if (h->opt.rows_per_item <= 0) {
+    // longest items (fewest re-shot first rows) that still give every
+    // resident warp >= 16 items to balance over
+    const int64_t rows = h->row_hi - h->row_lo, want = 16 * 8 * (int64_t)shoot_grid();
+    int rpi = 256;
+    while (rpi > 16 && (int64_t)M.strips * ((rows + rpi - 1) / rpi) < want) rpi >>= 1;
+    h->rows_per_item = rpi;
+  }
   M.rows_per_item = h->rows_per_item;
   M.row_blocks = (h->row_hi - h->row_lo + h->rows_per_item - 1) / h->rows_per_item;
   M.work_begin = 0;
@@ -549,7 +590,9 @@ static void fill_mapdev(mm_map *h) {
   M.near_pos = h->near_pos.p;
   M.near_m = h->near_m.p;
   M.coef = h->coef.p;
-  M.p = h->p;
+  M.p = h->p_eval;
+  M.sub = h->sub;
+  M.node_level = h->lvl.p;
   M.square_cells = (P.h[0] == P.h[1]) ? 1 : 0;
   const double ak = 1.0 - P.kappa + P.kappa_star;
   M.A1 = (float)((ak + P.gamma) * P.h[0] / P.delta);
@@ -561,14 +604,6 @@ static void fill_mapdev(mm_map *h) {
   M.acc = h->acc.p;
   M.span = h->span.p;
   M.stat = h->stat.p;
-}
-
-static int shoot_grid() {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  per_sm = MM_SHOOT_MINB;  // resident 256-thread blocks per SM
-  return std::max(1, sms * per_sm);
 }
 
 static mm_status clear_map(mm_map *h, cudaStream_t st) {
@@ -683,13 +718,15 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
     return fail(MM_EINVAL, "leaf_size %d outside [0, 1024]", leaf_size);
   if (h->opt.mode != MM_FMM_FP32 && h->opt.mode != MM_PLAIN_FP64)
     return fail(MM_EINVAL, "unknown mode %d", h->opt.mode);
+  if (h->opt.sub_levels < -1 || h->opt.sub_levels > MM_SUB_MAX)
+    return fail(MM_EINVAL, "sub_levels %d outside [-1, %d]", h->opt.sub_levels, MM_SUB_MAX);
   if (n_stars > 0 && !pos_xy) return fail(MM_EINVAL, "pos_xy is NULL");
   if (n_stars > 2000000000LL) return fail(MM_EINVAL, "too many stars");
   h->mode = h->opt.mode;
   h->p = fmm_order;
   h->leaf_size = leaf_size ? leaf_size : 32;
   h->N = n_stars;
-  h->rows_per_item = h->opt.rows_per_item > 0 ? std::min(h->opt.rows_per_item, 4096) : 64;
+  h->rows_per_item = h->opt.rows_per_item > 0 ? std::min(h->opt.rows_per_item, 4096) : 256;
 
   // cell-row band
   const int64_t rows = P.n[1] - 1;
@@ -957,6 +994,8 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
   out->params = h->P;
   out->mode = h->mode;
   out->fmm_order = h->mode == MM_FMM_FP32 ? h->p : 0;
+  out->eval_order = h->mode == MM_FMM_FP32 ? h->p_eval : 0;
+  out->sub_levels = h->mode == MM_FMM_FP32 ? h->sub : 0;
   out->leaf_size = h->leaf_size;
   out->depth = h->depth;
   out->n_stars = h->N;
@@ -976,11 +1015,9 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
     for (int32_t c : fc) leaves += (c < 0);
     out->leaves = leaves;
     // vertex-weighted mean near-field size over active leaves
-    std::vector<LeafRec> lr(h->n_active);
-    CK(cudaMemcpy(lr.data(), h->leaf.p, h->n_active * sizeof(LeafRec), cudaMemcpyDeviceToHost));
+    std::vector<LeafRec> lr(h->n_active << (2 * h->sub));
+    CK(cudaMemcpy(lr.data(), h->leaf.p, lr.size() * sizeof(LeafRec), cudaMemcpyDeviceToHost));
     double sw = 0.0, swn = 0.0;
-    const double L = 1.0;
-    (void)L;
     std::vector<int32_t> lv(h->n_nodes);
     CK(cudaMemcpy(lv.data(), h->lvl.p, h->n_nodes * sizeof(int32_t), cudaMemcpyDeviceToHost));
     for (const LeafRec &r : lr) {

@@ -243,33 +243,78 @@ __global__ void k_near_count(TreeDev T, int64_t n_active, const int32_t *active_
   near_cnt[t] = (int32_t)total;
 }
 
+// One thread per (active leaf t, sub-cell q).  The leaf's local expansion
+// psi = sum_l c_l zeta^l, zeta = (z - z_c)/L, is re-centred exactly on the
+// sub-cell centre z_q (an L2L translation to a descendant of the leaf, which
+// receives no further M2L terms: its far field is the leaf's):
+//   d_n = (L_q/L)^n sum_{l>=n} C(l, n) c_l u^(l-n),  u = (z_q - z_c)/L,
+// and kept to n <= p_eval.  The thread for q = 0 also writes the leaf's
+// near-field list, shared by all its sub-cells.  A record's coefficients
+// e_n = n d_n / (L_q delta), n = 2..p_eval, take coef_stride(p_eval) slots
+// (an even count, zero-padded) so the kernel loads them in pairs.
 __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_active,
                                 const int32_t *active_list, const int32_t *near_off,
-                                const double2 *__restrict__ loc, LeafRec *leaf,
-                                NearPos *near_pos, float *near_m, float2 *coef,
+                                const int32_t *near_cnt, const double2 *__restrict__ loc,
+                                LeafRec *leaf, NearPos *near_pos, float *near_m, float2 *coef,
                                 unsigned *err) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_active) return;
+  const int ns = 1 << C.sub, NS = ns * ns;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_active * NS) return;
+  const int64_t t = g / NS;
+  const int q = (int)(g % NS), qx = q & (ns - 1), qy = q >> C.sub;
   const int64_t node = active_list[t];
   int level, nx, ny;
   double zx, zy, L;
   node_geom(T, node, level, nx, ny, zx, zy, L);
-  const int p = C.p, P1 = p + 1;
+  const int p = C.p, P1 = p + 1, pe = C.p_eval, cs = coef_stride(pe);
 
-  // reference grid vertex nearest the centre
-  const double gi = rint((zx - C.x0) / C.hx), gj = rint((zy - C.y0) / C.hy);
+  // grid vertex nearest the leaf centre: frame of the near list
+  const double li = rint((zx - C.x0) / C.hx), lj = rint((zy - C.y0) / C.hy);
+  // the sub-cell and the grid vertex nearest its centre
+  const double ux = (double)(2 * qx + 1 - ns) / ns, uy = (double)(2 * qy + 1 - ns) / ns;
+  const double Lq = L / ns;
+  const double cx = zx + ux * L, cy = zy + uy * L;
+  const double gi = rint((cx - C.x0) / C.hx), gj = rint((cy - C.y0) / C.hy);
   const double xr = C.x0 + gi * C.hx, yr = C.y0 + gj * C.hy;
   LeafRec R;
   R.i_ref = (int32_t)gi;
   R.j_ref = (int32_t)gj;
-  R.fcx = (float)((zx - xr) / C.hx);
-  R.fcy = (float)((zy - yr) / C.hy);
+  R.fcx = (float)((cx - xr) / C.hx);
+  R.fcy = (float)((cy - yr) / C.hy);
+  R.offi = (float)(gi - li);
+  R.offj = (float)(gj - lj);
 
-  // FP64 image of the centre: macro model + sheet - far field at the centre
-  const double2 c1 = (p >= 1) ? loc[node * P1 + 1] : make_double2(0.0, 0.0);
+  // d_1 and the kept coefficients d_2..d_pe of the re-centred expansion
+  const double2 *c = loc + node * P1;
+  const double r = 1.0 / ns;
+  const double s = 1.0 / (Lq * C.delta);
+  double rn = 1.0;
+  double2 d1 = make_double2(0.0, 0.0);
+  for (int n = 1; n <= pe && n <= p; n++) {
+    rn *= r;
+    double sx = 0.0, sy = 0.0, px = 1.0, py = 0.0, binom = 1.0;  // u^(l-n), C(l, n)
+    for (int l = n; l <= p; l++) {
+      const double2 cl = c[l];
+      const double tx = cl.x * px - cl.y * py, ty = cl.x * py + cl.y * px;
+      sx += binom * tx;
+      sy += binom * ty;
+      const double npx = px * ux - py * uy;
+      py = px * uy + py * ux;
+      px = npx;
+      binom = binom * (double)(l + 1) / (double)(l + 1 - n);
+    }
+    const double2 dn = make_double2(sx * rn, sy * rn);
+    if (n == 1)
+      d1 = dn;
+    else
+      coef[g * cs + (n - 2)] = make_float2((float)(n * dn.x * s), (float)(n * dn.y * s));
+  }
+  for (int k = pe - 1; k < cs; k++) coef[g * cs + k] = make_float2(0.f, 0.f);
+
+  // FP64 image of the sub-cell centre: macro model + sheet - far field there
   const double ak = 1.0 - C.kappa + C.kappa_star;
-  const double Wx = (ak + C.gamma) * zx - c1.x / L;
-  const double Wy = (ak - C.gamma) * zy + c1.y / L;  // - conj(c1/L)
+  const double Wx = (ak + C.gamma) * cx - d1.x / Lq;
+  const double Wy = (ak - C.gamma) * cy + d1.y / Lq;  // - conj(d1/L_q)
   double U = (Wx - C.lox) / C.delta, V = (Wy - C.loy) / C.delta;
   // |Ui|, |Vi| < 2^28 keeps vertex pixel indices within +-2^29
   U = fmin(fmax(U, -2.0e8), 2.0e8);
@@ -279,20 +324,23 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_active,
   R.Vi = (int32_t)Vi;
   R.Uf = (float)(U - Ui);
   R.Vf = (float)(V - Vi);
-  R.zsx = (float)(C.hx / L);
-  R.zsy = (float)(C.hy / L);
+  R.zsx = (float)(C.hx / Lq);
+  R.zsy = (float)(C.hy / Lq);
   R.near_off = near_off[t];
-  R.coef_off = (int32_t)(t * (p > 1 ? p - 1 : 1));
+  R.near_cnt = near_cnt[t];
+  R.coef_off = (int32_t)(g * cs);
   R.node = (int32_t)node;
-  R.pad0 = R.pad1 = 0;
+  leaf[g] = R;
 
-  // near-field stars in the leaf's grid frame
+  if (q != 0) return;
+  // near-field stars in the frame of the vertex nearest the leaf centre
+  const double xl = C.x0 + li * C.hx, yl = C.y0 + lj * C.hy;
   int64_t k = R.near_off;
   for_each_near_range(
       T, node,
       [&](int64_t b, int64_t e) {
         for (int64_t i = b; i < e; i++) {
-          const double sxg = (T.sx[i] - xr) / C.hx, syg = (T.sy[i] - yr) / C.hy;
+          const double sxg = (T.sx[i] - xl) / C.hx, syg = (T.sy[i] - yl) / C.hy;
           const double Kx = rint(sxg), Ky = rint(syg);
           NearPos np;
           np.Kx = (float)Kx;
@@ -305,15 +353,6 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_active,
         }
       },
       err);
-  R.near_cnt = (int32_t)(k - R.near_off);
-  leaf[t] = R;
-
-  // far-field coefficients e_l = l c_l / (L delta), l = 2..p
-  const double s = 1.0 / (L * C.delta);
-  for (int l = 2; l <= p; l++) {
-    const double2 c = loc[node * P1 + l];
-    coef[R.coef_off + (l - 2)] = make_float2((float)(l * c.x * s), (float)(l * c.y * s));
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -433,12 +472,14 @@ cudaError_t launch_near_count(const TreeDev &T, int64_t n_active, const int32_t 
 
 cudaError_t launch_leaf_finalize(const TreeDev &T, const FmmConst &C, int64_t n_active,
                                  const int32_t *active_list, const int32_t *near_off,
-                                 const double2 *loc, LeafRec *leaf, NearPos *near_pos,
-                                 float *near_m, float2 *coef, unsigned *err, cudaStream_t st) {
+                                 const int32_t *near_cnt, const double2 *loc, LeafRec *leaf,
+                                 NearPos *near_pos, float *near_m, float2 *coef, unsigned *err,
+                                 cudaStream_t st) {
   if (n_active <= 0) return cudaSuccess;
-  k_leaf_finalize<<<blocks_for(n_active, 64), 64, 0, st>>>(T, C, n_active, active_list, near_off,
-                                                           loc, leaf, near_pos, near_m, coef,
-                                                           err);
+  const int64_t n = n_active << (2 * C.sub);
+  k_leaf_finalize<<<blocks_for(n, 64), 64, 0, st>>>(T, C, n_active, active_list, near_off,
+                                                    near_cnt, loc, leaf, near_pos, near_m, coef,
+                                                    err);
   return cudaGetLastError();
 }
 

@@ -39,9 +39,9 @@
 //     the pixel rows of 32 such triangles are dealt out to the lanes, each
 //     row adds the constant 1/|area| to its run of fully covered pixels
 //     through a per-row difference array, and the partially covered pixels
-//     of those rows are then dealt out one per lane and measured with the
-//     edge integrals of edge_band_integral.  Work is proportional to the
-//     perimeter, not the area, and no lane loops on its own.
+//     of those rows are then dealt out one per lane and measured from the
+//     row's edge pieces (edge_piece, piece_mean).  Work is proportional to
+//     the perimeter, not the area, and no lane loops on its own.
 #pragma once
 #include <climits>
 
@@ -321,7 +321,14 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   job.oy = oy;
 #pragma unroll
   for (int k = 0; k < 6; k++) job.t[k] = t[k];
-  job.inv2 = 2.0f / area2;
+  {
+    // 2 / area from the difference of products rounded once (Kahan's FMA
+    // method): the area of a long thin triangle cancels heavily in FP32
+    const float pa = t[2] - t[0], pd = t[5] - t[1], pb = t[4] - t[0], pc = t[3] - t[1];
+    const float wbc = pb * pc;
+    const float a2 = fmaf(pa, pd, -wbc) + fmaf(-pb, pc, wbc);
+    job.inv2 = 2.0f / ((a2 != 0.f && isfinite(a2)) ? a2 : area2);
+  }
 #pragma unroll
   for (int e = 0; e < 3; e++)
     job.k[e] = (t[(2 * e + 2) % 6] - t[2 * e]) / (t[(2 * e + 3) % 6] - t[2 * e + 1]);
@@ -337,42 +344,42 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
 // partially covered pixels of those rows
 // ---------------------------------------------------------------------------
 
-// Integral over y in [0, 1] of clamp(x(y), 0, 1) along the edge P -> Q
-// (pixel-local coordinates, k = dx/dy of the edge); signed by the direction
-// of y.  Summed over T's three edges this is area(T n [0, 1]^2), signed by
-// T's orientation (Green's theorem on the clamped boundary, as above).  The
-// x-average of clamp over [a, b] is formed from sub-interval lengths, so a
-// nearly vertical piece loses no precision.  x on the edge is extrapolated
-// from the nearer endpoint, which halves the error the rounding of k makes
-// on long edges.
+// Pixel areas of a larger triangle (Green's theorem on the clamped
+// boundary, as above): area(T n [0, 1]^2) is the sum over T's edges of the
+// integral over y in [0, 1] of clamp(x(y), 0, 1) along the edge, signed by
+// the direction of y.  The clamped y-range of an edge and its x there depend
+// only on the pixel row, so they are found once per row (edge_piece) and
+// each pixel of the row only shifts them by its column (piece_integral).
+
+// x on edge P -> Q (inverse slope k) at height y, extrapolated from the
+// nearer endpoint, which halves the error the rounding of k makes on long
+// edges.
 __device__ __forceinline__ float edge_x_at(float y, float px, float py, float qx, float qy,
                                           float k) {
   const float d1 = y - py, d2 = y - qy;
   return fabsf(d1) <= fabsf(d2) ? fmaf(d1, k, px) : fmaf(d2, k, qx);
 }
 
-__device__ __forceinline__ float edge_band_integral(float px, float py, float qx, float qy,
-                                                    float k) {
+// Piece of edge P -> Q (row-local coordinates) inside the band 0 <= y <= 1:
+// its x-range [a, b] and signed height h (all zero when it misses the band).
+__device__ __forceinline__ void edge_piece(float px, float py, float qx, float qy, float k,
+                                           float &a, float &b, float &h) {
   const float ys = fminf(fmaxf(py, 0.f), 1.f), ye = fminf(fmaxf(qy, 0.f), 1.f);
   const float xs = edge_x_at(ys, px, py, qx, qy, k), xe = edge_x_at(ye, px, py, qx, qy, k);
-  const float a = fminf(xs, xe), b = fmaxf(xs, xe);
+  const bool cross = ye != ys;
+  a = cross ? fminf(xs, xe) : 0.f;
+  b = cross ? fmaxf(xs, xe) : 0.f;
+  h = cross ? ye - ys : 0.f;
+}
+
+// Mean of clamp(x, 0, 1) over x in [a, b] (a piece shifted to its pixel),
+// formed from sub-interval lengths so that a nearly vertical piece loses no
+// precision; h times it is the piece's integral.
+__device__ __forceinline__ float piece_mean(float a, float b) {
   const float w = fminf(fmaxf(a, 0.f), 1.f), v = fminf(fmaxf(b, 0.f), 1.f);
   const float in = fmaf(0.5f * (v - w), v + w, fmaxf(b - fmaxf(a, 1.f), 0.f));
   const float len = b - a;
-  const float avg = len > 0.f ? in * rcp_approx_f(len) : w;
-  return ye != ys ? (ye - ys) * avg : 0.f;
-}
-
-// Share of triangle J in frame pixel (c, r).
-__device__ __forceinline__ float tri_pixel_fraction(const TriJob &J, int c, int r) {
-  const float fc = (float)c, fr = (float)r;
-  const float x0 = J.t[0] - fc, y0 = J.t[1] - fr;
-  const float x1 = J.t[2] - fc, y1 = J.t[3] - fr;
-  const float x2 = J.t[4] - fc, y2 = J.t[5] - fr;
-  const float s = edge_band_integral(x0, y0, x1, y1, J.k[0]) +
-                  edge_band_integral(x1, y1, x2, y2, J.k[1]) +
-                  edge_band_integral(x2, y2, x0, y0, J.k[2]);
-  return s * J.inv2;
+  return len > 0.f ? in * rcp_approx_f(len) : w;
 }
 
 // Frame row r of J: the columns [c0, c1] its band meets (widened by a small
@@ -434,14 +441,26 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
   return v;
 }
 
+// One pixel row of a larger triangle, shared by the lanes that measure its
+// partially covered pixels: for each edge its piece in the row band, x
+// relative to column c0, with height times 2/area (so the weighted sum of
+// piece means is the pixel's share); the global column of c0, the global
+// row, and the fully covered run [fa, fb] relative to c0 (none if fa > fb).
+struct __align__(16) RowRec {
+  float a[3], b[3], h[3];
+  int gx0, gy, fa, fb;
+  int pad[3];
+};
+
 // The nb (<= 32) triangles q[0..nb) (warp shared memory) spanning more than
 // 2 x 2 pixels.  Their pixel rows within the map are dealt out to the lanes,
 // 32 at a time; a row adds 1/|area| to its fully covered run through the
-// row difference array, and the partially covered pixels of those 32 rows
-// are then dealt out one per lane.  Work is proportional to the perimeter,
-// and the lanes stay busy however the rows differ.  Call with all 32 lanes.
+// row difference array and records its edge pieces in rr[lane]; the
+// partially covered pixels of those 32 rows are then dealt out one per lane.
+// Work is proportional to the perimeter, and the lanes stay busy however
+// the rows differ.  Call with all 32 lanes.
 static __device__ __noinline__ void warp_tri_jobs(const MapDev &M, const TriJob *q, int nb,
-                                                  int lane) {
+                                                  RowRec *rr, int lane) {
   int rl = 0, nrows = 0;
   if (lane < nb) {
     const TriJob &J = q[lane];
@@ -458,10 +477,10 @@ static __device__ __noinline__ void warp_tri_jobs(const MapDev &M, const TriJob 
     const int task = base + lane;
     const int k = scan_owner(incl, task);
     const int r = __shfl_sync(0xffffffffu, rl, k) + task - __shfl_sync(0xffffffffu, incl - nrows, k);
-    int c0 = 0, fa = 1, fb = 0, np = 0;
+    int np = 0;
     if (task < total) {
       const TriJob &J = q[k];
-      int c1;
+      int c0, c1, fa, fb;
       tri_row_extent(J, r, c0, c1, fa, fb);
       c0 = max(c0, -J.ox);
       c1 = min(c1, M.npix - 1 - J.ox);
@@ -478,29 +497,44 @@ static __device__ __noinline__ void warp_tri_jobs(const MapDev &M, const TriJob 
           atomicAdd(&sp[J.ox + fb + 1], 0ull - full);
         }
       }
+      if (np > 0) {
+        RowRec R;
+        const float fc0 = (float)c0, fr = (float)r;
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+          edge_piece(J.t[2 * e] - fc0, J.t[2 * e + 1] - fr, J.t[(2 * e + 2) % 6] - fc0,
+                     J.t[(2 * e + 3) % 6] - fr, J.k[e], R.a[e], R.b[e], R.h[e]);
+          R.h[e] *= J.inv2;
+        }
+        R.gx0 = J.ox + c0;
+        R.gy = J.oy + r;
+        R.fa = fa - c0;
+        R.fb = fb - c0;
+        R.pad[0] = R.pad[1] = R.pad[2] = 0;
+        rr[lane] = R;
+      }
     }
+    __syncwarp();
     // the partially covered pixels of these 32 rows
     const int pincl = warp_incl_scan(np, lane);
     const int ptotal = __shfl_sync(0xffffffffu, pincl, 31);
     for (int pbase = 0; pbase < ptotal; pbase += 32) {
       const int ptask = pbase + lane;
       const int j = scan_owner(pincl, ptask);
-      const int jk = __shfl_sync(0xffffffffu, k, j);
-      const int jr = __shfl_sync(0xffffffffu, r, j);
-      const int jc0 = __shfl_sync(0xffffffffu, c0, j);
-      const int jfa = __shfl_sync(0xffffffffu, fa, j);
-      const int jfb = __shfl_sync(0xffffffffu, fb, j);
       const int jst = __shfl_sync(0xffffffffu, pincl - np, j);
       if (ptask < ptotal) {
-        int c = jc0 + (ptask - jst);
-        if (jfa <= jfb && c >= jfa) c += jfb - jfa + 1;
-        const TriJob &J = q[jk];
-        deposit(M, (long long)J.ox + c, (long long)J.oy + jr,
-                frac_to_fixed(tri_pixel_fraction(J, c, jr)));
+        const RowRec &R = rr[j];
+        int c = ptask - jst;
+        if (R.fa <= R.fb && c >= R.fa) c += R.fb - R.fa + 1;
+        const float cl = (float)c;
+        float sh = 0.f;
+#pragma unroll
+        for (int e = 0; e < 3; e++) sh = fmaf(R.h[e], piece_mean(R.a[e] - cl, R.b[e] - cl), sh);
+        deposit(M, (long long)R.gx0 + c, R.gy, frac_to_fixed(sh));
       }
     }
+    __syncwarp();
   }
-  __syncwarp();
 }
 
 // Per-warp queue of larger triangles in shared memory (capacity 64 >=
@@ -508,13 +542,15 @@ static __device__ __noinline__ void warp_tri_jobs(const MapDev &M, const TriJob 
 // busy and the dealing overhead is amortised.
 struct JobQueue {
   TriJob *q;
+  RowRec *rr;
   int n;
 };
 
-// Shared memory of one warp: the two queues.
+// Shared memory of one warp: the two queues and the row records.
 struct WarpSmem {
   SmallTri quad[64];
   TriJob big[64];
+  RowRec rows[32];
 };
 #define MM_SHOOT_SMEM_BYTES (8 * sizeof(WarpSmem))  // 8 warps per block
 
@@ -528,12 +564,12 @@ __device__ __forceinline__ void jq_push(const MapDev &M, JobQueue &jq, bool want
   __syncwarp();
   while (jq.n >= 32) {
     jq.n -= 32;
-    warp_tri_jobs(M, jq.q + jq.n, 32, lane);
+    warp_tri_jobs(M, jq.q + jq.n, 32, jq.rr, lane);
   }
 }
 
 __device__ __forceinline__ void jq_drain(const MapDev &M, JobQueue &jq, int lane) {
-  if (jq.n > 0) warp_tri_jobs(M, jq.q, jq.n, lane);
+  if (jq.n > 0) warp_tri_jobs(M, jq.q, jq.n, jq.rr, lane);
   jq.n = 0;
   __syncwarp();
 }

@@ -11,6 +11,8 @@
 
 #define MM_DMAX 21            // deepest quadtree level
 #define MM_PMAX 64            // largest expansion order accepted by the ABI
+#define MM_SUB_MAX 2          // largest sub-cell level count (16 sub-cells per leaf)
+#define MM_SUB_DEFAULT 2      // sub-cell levels when the options leave it to the library
 #define MM_STRIP 31           // cell columns per warp work item (32 vertex columns)
 #define MM_MED_PIXELS 64      // bounding box (map pixels) up to which a larger
                               // triangle is counted as medium in the statistics
@@ -23,24 +25,27 @@ enum : unsigned int {
   ERR_LOOKUP = 2u,            // a ray vertex fell outside every active leaf
 };
 
-// Per active leaf: everything a ray vertex in the leaf needs (64 bytes).
-// Positions inside the leaf are measured in ray-grid units from the grid
-// vertex (i_ref, j_ref) closest to the leaf centre; the leaf centre sits at
-// (i_ref + fcx, j_ref + fcy) in those units.
+// Per sub-cell of an active leaf: everything a ray vertex in it needs (64
+// bytes).  Each active leaf t owns the 4^s records [4^s t, 4^s (t + 1)), one
+// per sub-cell of side 2 L / 2^s (s = MapDev::sub, row-major, y major); the
+// leaf's local expansion is re-centred on each sub-cell.  Positions are
+// measured in ray-grid units from the grid vertex (i_ref, j_ref) closest to
+// the sub-cell centre, which sits at (i_ref + fcx, j_ref + fcy).
 struct __align__(16) LeafRec {
   int32_t i_ref, j_ref;
   float fcx, fcy;
   int32_t Ui, Vi;             // integer part of the centre's image in pixels
   float Uf, Vf;               // fractional part (FP64-accurate)
-  float zsx, zsy;             // h_x / L, h_y / L : grid units -> zeta units
-  int32_t near_off, near_cnt; // near-field stars in MapDev::near_pos/near_m
-  int32_t coef_off;           // first of (p - 1) far-field coefficients
-  int32_t node;               // tree node id
-  int32_t pad0, pad1;
+  float zsx, zsy;             // h_x / L_s, h_y / L_s : grid units -> zeta units
+  int32_t near_off, near_cnt; // the leaf's near-field stars in near_pos/near_m
+  int32_t coef_off;           // first of coef_stride(p_eval) far-field coefficient slots
+  int32_t node;               // tree node id of the leaf
+  float offi, offj;           // (i_ref, j_ref) minus the near list's reference vertex
 };
 
-// Near-field star in the leaf's grid frame: grid position relative to
-// (i_ref, j_ref) = (Kx + fx, Ky + fy), K integer-valued, |f| <= 0.5.
+// Near-field star in the leaf's grid frame: grid position relative to the
+// grid vertex closest to the leaf centre = (Kx + fx, Ky + fy), K
+// integer-valued, |f| <= 0.5.
 struct __align__(16) NearPos {
   float Kx, fx, Ky, fy;
 };
@@ -63,16 +68,18 @@ struct MapDev {
   int64_t work_begin;         // first global work item of this map
   // leaf lookup
   const int32_t *col_cell, *row_cell;   // finest-level cell index per vertex column / row
-  const int32_t *grid;                  // lookup grid: active leaf id, or -(node+1)
+  const int32_t *grid;                  // lookup grid: sub-cell record id, or -(node+1)
   int32_t glevel, gshift, gx0, gy0, gw, gh;
   const int32_t *first_child;           // per node: first child id, -1 for a leaf
   const int32_t *node_active;           // per node: active leaf id or -1
+  const int32_t *node_level;            // per node: tree level
+  int32_t sub;                          // sub-cell levels s (4^s records per leaf)
   // leaves
   const LeafRec *leaf;
   const NearPos *near_pos;
   const float *near_m;
   const float2 *coef;
-  int32_t p;                  // expansion order
+  int32_t p;                  // terms of the re-centred expansion evaluated per ray
   int32_t square_cells;       // 1 when h_x == h_y
   // per-ray constants (pixel units)
   float A1, A2;               // (1 - kappa + kappa_star +- gamma) h / delta
@@ -85,6 +92,12 @@ struct MapDev {
   // statistics (per map)
   unsigned long long *stat;   // triangle counters, see IpmCounters
 };
+
+// Far-field coefficient slots per sub-cell record: the p_eval - 1
+// coefficients rounded up to an even count (>= 2), loaded as float4 pairs.
+__host__ __device__ __forceinline__ int coef_stride(int p_eval) {
+  return p_eval <= 2 ? 2 : ((p_eval - 1 + 1) & ~1);
+}
 
 // Interleave two 21-bit integers: x in even bits, y in odd bits.
 __host__ __device__ __forceinline__ uint64_t morton2(uint32_t x, uint32_t y) {

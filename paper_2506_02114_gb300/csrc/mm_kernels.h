@@ -52,12 +52,14 @@ cudaError_t launch_compact_leaves(int64_t n_nodes, const int32_t *leaf_flag,
                                   const int32_t *leaf_scan, int32_t *node_active,
                                   int32_t *active_list, cudaStream_t st);
 cudaError_t launch_lookup_grid(const TreeDev &T, const int32_t *node_active, int glevel,
-                               int gx0, int gy0, int gw, int gh, int32_t *grid,
+                               int sub, int gx0, int gy0, int gw, int gh, int32_t *grid,
                                cudaStream_t st);
 
 // ---- expansions (fmm.cu) ---------------------------------------------------
 struct FmmConst {
-  int p;
+  int p;                      // expansion order of the FMM
+  int p_eval;                 // terms kept of each sub-cell's re-centred expansion
+  int sub;                    // sub-cell levels s: 4^s sub-cells per leaf
   double kappa, gamma, kappa_star;
   double x0, y0, hx, hy;      // ray grid
   double lox, loy, delta;     // map lower-left corner and pixel side
@@ -73,6 +75,7 @@ cudaError_t launch_near_count(const TreeDev &T, int64_t n_active, const int32_t 
                               int32_t *near_cnt, unsigned *err, cudaStream_t st);
 cudaError_t launch_leaf_finalize(const TreeDev &T, const FmmConst &C, int64_t n_active,
                                  const int32_t *active_list, const int32_t *near_off,
+                                 const int32_t *near_cnt,
                                  const double2 *loc, LeafRec *leaf, NearPos *near_pos,
                                  float *near_m, float2 *coef, unsigned *err, cudaStream_t st);
 void build_operator_tables(int p, std::vector<double2> &MM, std::vector<double2> &ML,

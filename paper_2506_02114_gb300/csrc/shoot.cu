@@ -23,7 +23,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Active leaf containing finest-level cell (cx, cy); -1 if none.
+// Record of the sub-cell of the active leaf containing finest-level cell
+// (cx, cy); -1 if none.
 __device__ __forceinline__ int lookup_leaf(const MapDev &M, int cx, int cy) {
   int gx = (cx >> M.gshift) - M.gx0, gy = (cy >> M.gshift) - M.gy0;
   if (gx < 0 || gy < 0 || gx >= M.gw || gy >= M.gh) return -1;
@@ -36,7 +37,11 @@ __device__ __forceinline__ int lookup_leaf(const MapDev &M, int cx, int cy) {
     int sh = MM_DMAX - lvl;
     node = fc + (((cx >> sh) & 1) | (((cy >> sh) & 1) << 1));
   }
-  return __ldg(&M.node_active[node]);
+  const int a = __ldg(&M.node_active[node]);
+  if (a < 0) return -1;
+  // the host keeps every leaf level + sub <= MM_DMAX
+  const int sh = MM_DMAX - __ldg(&M.node_level[node]) - M.sub, mask = (1 << M.sub) - 1;
+  return (a << (2 * M.sub)) + (((cy >> sh) & mask) << M.sub) + ((cx >> sh) & mask);
 }
 
 // Source-plane position of grid point (i + ti, j + tj) in pixel units:
@@ -53,11 +58,14 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
   const float zsx = __int_as_float(q2.x), zsy = __int_as_float(q2.y);
   const int near_off = q2.z, near_cnt = (leaf < 0) ? 0 : q2.w;
   const int coef_off = q3.x;
+  const float offi = __int_as_float(q3.z), offj = __int_as_float(q3.w);
 
   // vertex position relative to the reference vertex, in grid units (exact
   // integers), and relative to the leaf centre
   const float fi = (float)(int)(i - i_ref), fj = (float)(int)(j - j_ref);
   float gx = fi - fcx, gy = fj - fcy;
+  // the same vertex in the near list's frame (integers, exact)
+  const float ni = fi + offi, nj = fj + offj;
   if (FRAC) {
     gx += ti;
     gy += tj;
@@ -75,8 +83,8 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
     const float4 s0 = a0 ? __ldg(np_ + k) : make_float4(0.f, 1.f, 0.f, 0.f);
     const float4 s1 = a1 ? __ldg(np_ + k + 1) : make_float4(0.f, 1.f, 0.f, 0.f);
     const float m0 = a0 ? __ldg(nm_ + k) : 0.f, m1 = a1 ? __ldg(nm_ + k + 1) : 0.f;
-    float dx0 = (fi - s0.x) - s0.y, dy0 = (fj - s0.z) - s0.w;
-    float dx1 = (fi - s1.x) - s1.y, dy1 = (fj - s1.z) - s1.w;
+    float dx0 = (ni - s0.x) - s0.y, dy0 = (nj - s0.z) - s0.w;
+    float dx1 = (ni - s1.x) - s1.y, dy1 = (nj - s1.z) - s1.w;
     if (FRAC) {
       dx0 += ti;
       dy0 += tj;
@@ -94,7 +102,7 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
   if (k < maxcnt && k < near_cnt) {
     const float4 s0 = __ldg(np_ + k);
     const float m0 = __ldg(nm_ + k);
-    float dx0 = (fi - s0.x) - s0.y, dy0 = (fj - s0.z) - s0.w;
+    float dx0 = (ni - s0.x) - s0.y, dy0 = (nj - s0.z) - s0.w;
     if (FRAC) {
       dx0 += ti;
       dy0 += tj;
@@ -107,26 +115,30 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
   Sx += Sx2;
   Sy += Sy2;
 
-  // far field: f = sum_{l=2}^{p} e_l zeta^(l-1), e_l = l c_l / (L delta)
+  // far field: f = sum_{k>=0} e_k zeta^(k+1), e_k = (k+2) c_(k+2) / (L delta),
+  // as zeta E(w) + w O(w), w = zeta^2, E and O the even and odd k: two
+  // independent Horner chains, one (e_2j, e_2j+1) pair per 16-byte load
   float fr = 0.f, fim = 0.f;
-  const int p = M.p;
-  if (p >= 2 && leaf >= 0) {
+  const int npair = M.p >> 1;
+  if (npair >= 1 && leaf >= 0) {
     const float zx = gx * zsx, zy = gy * zsy;
-    const float2 *e = M.coef + coef_off;
-    float2 t = __ldg(e + (p - 2));
-    fr = t.x;
-    fim = t.y;
-    for (int l = p - 3; l >= 0; l--) {
-      float2 c = __ldg(e + l);
-      float nr = fmaf(fr, zx, fmaf(-fim, zy, c.x));
-      float ni = fmaf(fr, zy, fmaf(fim, zx, c.y));
-      fr = nr;
-      fim = ni;
+    const float wx = fmaf(zx, zx, -zy * zy), wy = 2.f * zx * zy;
+    const float4 *e = reinterpret_cast<const float4 *>(M.coef + coef_off);
+    float4 c = __ldg(e + (npair - 1));
+    float Er = c.x, Ei = c.y, Or = c.z, Oi = c.w;
+    for (int j = npair - 2; j >= 0; j--) {
+      c = __ldg(e + j);
+      const float er = fmaf(Er, wx, fmaf(-Ei, wy, c.x));
+      const float ei = fmaf(Er, wy, fmaf(Ei, wx, c.y));
+      const float orr = fmaf(Or, wx, fmaf(-Oi, wy, c.z));
+      const float oi = fmaf(Or, wy, fmaf(Oi, wx, c.w));
+      Er = er;
+      Ei = ei;
+      Or = orr;
+      Oi = oi;
     }
-    float nr = fr * zx - fim * zy;
-    float ni = fr * zy + fim * zx;
-    fr = nr;
-    fim = ni;
+    fr = fmaf(zx, Er, fmaf(-zy, Ei, fmaf(wx, Or, -wy * Oi)));
+    fim = fmaf(zx, Ei, fmaf(zy, Er, fmaf(wx, Oi, wy * Or)));
   }
 
   float u = Uf + (fmaf(M.A1, gx, -Sx * M.sx) - fr);
@@ -189,7 +201,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
   extern __shared__ __align__(16) unsigned char s_dyn[];
   WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
   WarpQueue wq = {ws->quad, 0};
-  JobQueue jq = {ws->big, 0};
+  JobQueue jq = {ws->big, ws->rows, 0};
   IpmCounters cnt = {0, 0, 0, 0, 0, 0};
   int last_map = -1;
   while (true) {

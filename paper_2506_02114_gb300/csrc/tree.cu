@@ -153,19 +153,29 @@ __global__ void k_compact_leaves(int64_t n_nodes, const int32_t *leaf_flag,
 
 // Lookup grid over the active region at level glevel: the active leaf
 // covering each cell, or -(node + 1) for a split node at glevel.
-__global__ void k_lookup_grid(TreeDev T, const int32_t *node_active, int glevel, int gx0, int gy0,
-                              int gw, int gh, int32_t *grid) {
+// Grid cell (gx, gy) of level glevel: the sub-cell record of the active leaf
+// containing it when the leaf is at least `sub` levels coarser (the cell then
+// lies in one sub-cell), else -(node + 1) for the node where the device walk
+// continues.
+__global__ void k_lookup_grid(TreeDev T, const int32_t *node_active, int glevel, int sub,
+                              int gx0, int gy0, int gw, int gh, int32_t *grid) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)gw * gh) return;
   const int gx = gx0 + (int)(t % gw), gy = gy0 + (int)(t / gw);
-  int node = 0;
-  for (int l = 0; l < glevel; l++) {
+  int node = 0, l = 0;
+  for (; l < glevel; l++) {
     int fc = T.first_child[node];
     if (fc < 0) break;
     int sh = glevel - l - 1;
     node = fc + (((gx >> sh) & 1) | (((gy >> sh) & 1) << 1));
   }
-  grid[t] = (T.first_child[node] < 0) ? node_active[node] : -(node + 1);
+  const int a = (T.first_child[node] < 0) ? node_active[node] : -1;
+  if (a >= 0 && l + sub <= glevel) {
+    const int sh = glevel - l - sub, mask = (1 << sub) - 1;
+    grid[t] = (a << (2 * sub)) + (((gy >> sh) & mask) << sub) + ((gx >> sh) & mask);
+  } else {
+    grid[t] = -(node + 1);
+  }
 }
 
 static inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -236,12 +246,12 @@ cudaError_t launch_compact_leaves(int64_t n_nodes, const int32_t *leaf_flag,
 }
 
 cudaError_t launch_lookup_grid(const TreeDev &T, const int32_t *node_active, int glevel,
-                               int gx0, int gy0, int gw, int gh, int32_t *grid,
+                               int sub, int gx0, int gy0, int gw, int gh, int32_t *grid,
                                cudaStream_t st) {
   int64_t n = (int64_t)gw * gh;
   if (n <= 0) return cudaSuccess;
-  k_lookup_grid<<<blocks_for(n, 256), 256, 0, st>>>(T, node_active, glevel, gx0, gy0, gw, gh,
-                                                    grid);
+  k_lookup_grid<<<blocks_for(n, 256), 256, 0, st>>>(T, node_active, glevel, sub, gx0, gy0, gw,
+                                                    gh, grid);
   return cudaGetLastError();
 }
 

@@ -81,14 +81,19 @@ def test_point_lens_map(oracle_mod, mode):
     assert st["triangles_dropped"] == st_ref["dropped"]
 
 
+@pytest.mark.parametrize("sub_levels", [-1, 1, 2])
 @pytest.mark.parametrize("order", [8, 16, 25])
-def test_fmm_deflection_vs_direct_sum(oracle_mod, order):
+def test_fmm_deflection_vs_direct_sum(oracle_mod, order, sub_levels):
+    """FMM deflection against the direct sum at random points, with the local
+    expansions evaluated about the leaf centres (-1) or re-centred on 4 or
+    16 sub-cells per leaf with the correspondingly fewer terms."""
     kappa, gamma, s = 0.5, 0.4, 0.5
     m, pos = small_field(11, kappa, gamma, s, hl=2.0, npix=64, rpp=4.0,
                          mass_fn=synthetic.SALPETER_01_1)
     p = oracle_mod.derive_params(kappa, gamma, s, m, 2.0, 64, rays_per_pixel=4.0,
                                  flux_fraction_f=0.01)
-    h = mm.create(kappa, gamma, s, m, pos, 2.0, 64, fmm_order=order, **explicit_grid(p))
+    h = mm.create(kappa, gamma, s, m, pos, 2.0, 64, fmm_order=order, sub_levels=sub_levels,
+                  **explicit_grid(p))
     rng = np.random.default_rng(5)
     z = np.stack([rng.uniform(p.x0[0], p.x0[0] + (p.n[0] - 1) * p.h[0], 20000),
                   rng.uniform(p.x0[1], p.x0[1] + (p.n[1] - 1) * p.h[1], 20000)], 1)
@@ -99,6 +104,10 @@ def test_fmm_deflection_vs_direct_sum(oracle_mod, order):
     err = deflection_rel_error(p, z, w, w_ref)
     assert np.isfinite(w).all()
     assert st["depth"] >= 3
+    assert st["sub_levels"] == max(sub_levels, 0)
+    assert st["eval_order"] <= order
+    if order == 25:
+        assert st["eval_order"] == {-1: 25, 1: 15, 2: 11}[sub_levels]
     # truncation error falls with the order; at p = 25 the FP32 per-ray
     # arithmetic dominates and meets the deflection tolerance
     bound = {8: 2e-3, 16: 1e-4, 25: DEFLECTION_TOL}[order]
