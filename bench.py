@@ -3,7 +3,7 @@
 Workload (synthetic, seeded): kappa = 0.5, gamma = 0.4, s = 0.5, Salpeter
 masses 0.1-1 uniform in a disk of radius 212 (50 295 stars), 2000^2-pixel map
 of half-width 10, 9 rays per pixel without lensing (~100 landing per pixel),
-FMM order 25: a 12 793 x 115 309 ray grid (1.48e9 rays).
+FMM order 25: a 12 803 x 115 219 ray grid (1.475e9 rays).
 
 A step is one mm_run: Morton sort, quadtree, expansions, fused deflection +
 inverse polygon mapping, normalisation, with the stars already on the device.
@@ -41,7 +41,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FMA lanes x 2 flops 
 
 # dram bytes per launch of k_shoot_ipm from one ncu capture (see profiles/),
 # valid only for the kernel sources it was taken on (hash below)
-NCU_TRAFFIC = {"sources_sha1": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"sources_sha1": "19c54372c9e385881dda60a8a69bd74212ccb9cb",
+               "bytes_per_launch": 75.86e6 + 4.80e9}
 
 
 def kernel_sources_sha1():
@@ -294,8 +295,9 @@ def run_native(args):
                "includes": "mm_create (stars H2D, plan) + mm_run + mm_get_map (D2H) + mm_destroy"}
 
     # roofline of the hot kernel (FP32 ALU bound)
-    p = st["fmm_order"]
-    flops_per_ray = 11.0 * st["mean_near_stars"] + 8.0 * (p - 1) + 8.0 + 20.0
+    p, pe = st["fmm_order"], st["eval_order"]
+    # near field + local expansion (p_e terms about the sub-cell centre) + macro + IPM test
+    flops_per_ray = 11.0 * st["mean_near_stars"] + 8.0 * (pe - 1) + 8.0 + 20.0
     shoot_s = float(np.mean(shoot_ms)) * 1e-3
     achieved = rays * flops_per_ray / shoot_s / 1e12
     traffic = None
@@ -328,6 +330,7 @@ def run_native(args):
                    "n_stars": len(m), "mass_function": wl.mass_fn.name, "npix": wl.npix,
                    "half_length": wl.half_length, "rays_per_pixel": wl.rays_per_pixel,
                    "ray_grid": st["params"]["n"], "rays": rays, "fmm_order": p,
+                   "eval_order": pe, "sub_levels": st["sub_levels"],
                    "leaf_size": st["leaf_size"], "l2": "flushed before every step (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "maps_per_s": world / (ms_per_step * 1e-3),

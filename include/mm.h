@@ -121,7 +121,8 @@ typedef struct {
                                vertex, weighted by vertices */
   int64_t rays;             /* grid vertices shot by mm_run (band included) */
   int64_t cells;            /* grid cells mapped by mm_run */
-  int64_t triangles_dropped;/* zero-area or non-finite triangles (last run) */
+  int64_t triangles_dropped;/* non-finite triangles, and zero-area ones whose
+                               box meets the map (last run) */
   int64_t triangles_clipped;/* triangles spanning more than one pixel of the map */
   int64_t triangles_line;   /*   of which two pixels split by one grid line */
   int64_t triangles_quad;   /*   of which 2 x 2 pixels (both grid lines crossed) */

@@ -263,16 +263,17 @@ static void apportion_triangle(const double *tri, int npix, double *acc,
       st->dropped++;
       return;
     }
+  double xmin = fmin(tri[0], fmin(tri[2], tri[4]));
+  double xmax = fmax(tri[0], fmax(tri[2], tri[4]));
+  double ymin = fmin(tri[1], fmin(tri[3], tri[5]));
+  double ymax = fmax(tri[1], fmax(tri[3], tri[5]));
+  /* wholly outside the map: nothing to apportion (not counted as dropped) */
+  if (xmax < 0 || ymax < 0 || xmin >= npix || ymin >= npix) return;
   double area_t = shoelace(tri, 3);
   if (area_t == 0.0) {
     st->dropped++;
     return;
   }
-  double xmin = fmin(tri[0], fmin(tri[2], tri[4]));
-  double xmax = fmax(tri[0], fmax(tri[2], tri[4]));
-  double ymin = fmin(tri[1], fmin(tri[3], tri[5]));
-  double ymax = fmax(tri[1], fmax(tri[3], tri[5]));
-  if (xmax < 0 || ymax < 0 || xmin >= npix || ymin >= npix) return;
   int64_t px0 = (int64_t)floor(xmin), px1 = (int64_t)floor(xmax);
   int64_t py0 = (int64_t)floor(ymin), py1 = (int64_t)floor(ymax);
   if (px0 < 0) px0 = 0;

@@ -57,7 +57,8 @@ typedef struct {
 
 typedef struct {
   int64_t triangles;          /* triangles processed */
-  int64_t dropped;            /* zero-area or non-finite triangles */
+  int64_t dropped;            /* non-finite triangles, and zero-area ones whose
+                                 bounding box meets the map */
   int64_t pieces;             /* non-empty triangle/pixel intersections */
 } or_map_stats;
 

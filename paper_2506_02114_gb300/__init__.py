@@ -285,6 +285,18 @@ def map_plain_fp64_noalloc(kappa, gamma, s, masses_dev, pos_dev, half_length, np
     return map_out_dev
 
 
+def shard_rows(n_rows, rank, world):
+    """Cell rows [begin, end) of `rank` when one map's n_rows cell rows are
+    split over `world` ranks in contiguous bands (the first n_rows % world
+    bands one row longer).  Each rank maps its band (``row_begin/row_end``);
+    the fixed-point maps of the bands add up exactly to the whole map."""
+    if world < 1 or not 0 <= rank < world or n_rows < 0:
+        raise ValueError("bad shard request")
+    q, r = divmod(int(n_rows), int(world))
+    begin = rank * q + min(rank, r)
+    return begin, begin + q + (1 if rank < r else 0)
+
+
 def get_stats(h: Handle) -> dict:
     s = Stats()
     _check(lib().mm_get_stats(h.ptr, ctypes.byref(s)))

@@ -628,6 +628,7 @@ static mm_status alloc_map_buffers(mm_map *h) {
   CK(h->stat.ensure(8));
   CK(h->counter.ensure(1));
   CK(h->err.ensure(1));
+  CK(cudaMemset(h->err.p, 0, sizeof(unsigned)));  // read after the plan in every mode
   CK(h->d_md.ensure(1));
   return MM_OK;
 }

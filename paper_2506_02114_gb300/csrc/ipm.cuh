@@ -237,6 +237,11 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     cnt.dropped++;
     return TRI_DONE;
   }
+  // wholly beyond one edge of the map (most triangles of a shooting region):
+  // integer tests on the vertices' pixels, before any arithmetic
+  if (max(a.px, max(b.px, c.px)) < 0 || min(a.px, min(b.px, c.px)) >= M.npix ||
+      max(a.py, max(b.py, c.py)) < 0 || min(a.py, min(b.py, c.py)) >= M.npix)
+    return TRI_DONE;
   const int ox = a.px, oy = a.py;
   float t[6];
   t[0] = a.fx;
@@ -249,6 +254,11 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   const float area2 = (t[2] - t[0]) * (t[5] - t[1]) - (t[4] - t[0]) * (t[3] - t[1]);
   if (!(area2 != 0.f) || !isfinite(area2)) {
     cnt.dropped++;
+    return TRI_DONE;
+  }
+  if (a.px == b.px && a.px == c.px && a.py == b.py && a.py == c.py) {
+    // all three vertices in one (closed) map pixel: all of the area is there
+    run_add(M, ra, (long long)oy * M.npix + ox, MM_FIX_ONE);
     return TRI_DONE;
   }
   const float xmin = fminf(t[0], fminf(t[2], t[4])), xmax = fmaxf(t[0], fmaxf(t[2], t[4]));
