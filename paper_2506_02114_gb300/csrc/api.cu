@@ -675,7 +675,7 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     CKS(prepare(h, st));
     CKS(record(h, 2, st));
     const int64_t work = (int64_t)h->md.strips * h->md.row_blocks;
-    LCH(launch_shoot_ipm(h->d_md.p, 1, work, h->md.square_cells != 0, h->counter.p, h->err.p,
+    LCH(launch_shoot_ipm(h->d_md.p, &h->md, 1, work, h->md.square_cells != 0, h->counter.p, h->err.p,
                         shoot_grid(), st));
   }
   CKS(record(h, 3, st));
@@ -882,7 +882,7 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
   CK(lead->batch_md.ensure(n));
   CK(cudaMemcpyAsync(lead->batch_md.p, mds.data(), n * sizeof(MapDev), cudaMemcpyHostToDevice,
                      st));
-  CK(launch_shoot_ipm(lead->batch_md.p, n, work, all_square, lead->counter.p, lead->err.p,
+  CK(launch_shoot_ipm(lead->batch_md.p, nullptr, n, work, all_square, lead->counter.p, lead->err.p,
                       shoot_grid(), st));
   lead->launches++;
   for (int i = 0; i < n; i++) {

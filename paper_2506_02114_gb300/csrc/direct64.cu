@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
   extern __shared__ __align__(16) unsigned char s_dyn[];
   WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
   WarpQueue wq = {ws->quad, 0};
-  JobQueue jq = {ws->big, ws->rows, 0};
+  JobQueue jq = {ws->big, &ws->rows, 0};
   const MapDev &M = maps[0];
   const int64_t strips = (n0 - 1 + MM_STRIP - 1) / MM_STRIP;
   const int64_t rows = row_hi - row_lo;  // cell rows

@@ -78,6 +78,14 @@ __device__ __forceinline__ void deposit(const MapDev &M, long long gx, long long
     atomicAdd(&M.acc[gy * M.npix + gx], v);
 }
 
+// The map's accumulators alone, passed as scalars to the out-of-line row
+// and pixel dealing (so the kernel's MapDev, a launch parameter, is never
+// copied to local memory to be addressed).
+struct MapAcc {
+  unsigned long long *acc, *span;
+  int npix;
+};
+
 // Lane-private run accumulator: consecutive one-pixel triangles of a lane's
 // column usually hit the same pixel; they are summed in a register.
 struct RunAcc {
@@ -451,15 +459,16 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
   return v;
 }
 
-// One pixel row of a larger triangle, shared by the lanes that measure its
-// partially covered pixels: for each edge its piece in the row band, x
-// relative to column c0, with height times 2/area (so the weighted sum of
-// piece means is the pixel's share); the global column of c0, the global
-// row, and the fully covered run [fa, fb] relative to c0 (none if fa > fb).
-struct __align__(16) RowRec {
-  float a[3], b[3], h[3];
-  int gx0, gy, fa, fb;
-  int pad[3];
+// The pixel rows of one round of a larger-triangle batch, one per lane,
+// shared by the lanes that measure their partially covered pixels: for each
+// edge its piece in the row band, x relative to column c0, with height
+// times 2/area (so the weighted sum of piece means is the pixel's share);
+// the global column of c0, the global row, and the fully covered run
+// [fa, fb] relative to c0 (none if fa > fb).  Stored as arrays over lanes,
+// so lanes reading different rows hit different banks.
+struct RowRecs {
+  float a[3][32], b[3][32], h[3][32];
+  int gx0[32], gy[32], fa[32], fb[32];
 };
 
 // The nb (<= 32) triangles q[0..nb) (warp shared memory) spanning more than
@@ -469,8 +478,11 @@ struct __align__(16) RowRec {
 // partially covered pixels of those 32 rows are then dealt out one per lane.
 // Work is proportional to the perimeter, and the lanes stay busy however
 // the rows differ.  Call with all 32 lanes.
-static __device__ __noinline__ void warp_tri_jobs(const MapDev &M, const TriJob *q, int nb,
-                                                  RowRec *rr, int lane) {
+static __device__ __noinline__ void warp_tri_jobs(unsigned long long *acc,
+                                                  unsigned long long *span, int npix,
+                                                  const TriJob *q, int nb, RowRecs *rr,
+                                                  int lane) {
+  const MapAcc M = {acc, span, npix};
   int rl = 0, nrows = 0;
   if (lane < nb) {
     const TriJob &J = q[lane];
@@ -508,20 +520,20 @@ static __device__ __noinline__ void warp_tri_jobs(const MapDev &M, const TriJob 
         }
       }
       if (np > 0) {
-        RowRec R;
         const float fc0 = (float)c0, fr = (float)r;
 #pragma unroll
         for (int e = 0; e < 3; e++) {
+          float a, b, h;
           edge_piece(J.t[2 * e] - fc0, J.t[2 * e + 1] - fr, J.t[(2 * e + 2) % 6] - fc0,
-                     J.t[(2 * e + 3) % 6] - fr, J.k[e], R.a[e], R.b[e], R.h[e]);
-          R.h[e] *= J.inv2;
+                     J.t[(2 * e + 3) % 6] - fr, J.k[e], a, b, h);
+          rr->a[e][lane] = a;
+          rr->b[e][lane] = b;
+          rr->h[e][lane] = h * J.inv2;
         }
-        R.gx0 = J.ox + c0;
-        R.gy = J.oy + r;
-        R.fa = fa - c0;
-        R.fb = fb - c0;
-        R.pad[0] = R.pad[1] = R.pad[2] = 0;
-        rr[lane] = R;
+        rr->gx0[lane] = J.ox + c0;
+        rr->gy[lane] = J.oy + r;
+        rr->fa[lane] = fa - c0;
+        rr->fb[lane] = fb - c0;
       }
     }
     __syncwarp();
@@ -533,14 +545,17 @@ static __device__ __noinline__ void warp_tri_jobs(const MapDev &M, const TriJob 
       const int j = scan_owner(pincl, ptask);
       const int jst = __shfl_sync(0xffffffffu, pincl - np, j);
       if (ptask < ptotal) {
-        const RowRec &R = rr[j];
+        const int fa = rr->fa[j], fb = rr->fb[j];
         int c = ptask - jst;
-        if (R.fa <= R.fb && c >= R.fa) c += R.fb - R.fa + 1;
+        if (fa <= fb && c >= fa) c += fb - fa + 1;
         const float cl = (float)c;
         float sh = 0.f;
 #pragma unroll
-        for (int e = 0; e < 3; e++) sh = fmaf(R.h[e], piece_mean(R.a[e] - cl, R.b[e] - cl), sh);
-        deposit(M, (long long)R.gx0 + c, R.gy, frac_to_fixed(sh));
+        for (int e = 0; e < 3; e++)
+          sh = fmaf(rr->h[e][j], piece_mean(rr->a[e][j] - cl, rr->b[e][j] - cl), sh);
+        // the row and its columns lie in the map (clamped above)
+        const unsigned long long v = frac_to_fixed(sh);
+        if (v) atomicAdd(&M.acc[(long long)rr->gy[j] * M.npix + rr->gx0[j] + c], v);
       }
     }
     __syncwarp();
@@ -552,7 +567,7 @@ static __device__ __noinline__ void warp_tri_jobs(const MapDev &M, const TriJob 
 // busy and the dealing overhead is amortised.
 struct JobQueue {
   TriJob *q;
-  RowRec *rr;
+  RowRecs *rr;
   int n;
 };
 
@@ -560,7 +575,7 @@ struct JobQueue {
 struct WarpSmem {
   SmallTri quad[64];
   TriJob big[64];
-  RowRec rows[32];
+  RowRecs rows;
 };
 #define MM_SHOOT_SMEM_BYTES (8 * sizeof(WarpSmem))  // 8 warps per block
 
@@ -574,12 +589,12 @@ __device__ __forceinline__ void jq_push(const MapDev &M, JobQueue &jq, bool want
   __syncwarp();
   while (jq.n >= 32) {
     jq.n -= 32;
-    warp_tri_jobs(M, jq.q + jq.n, 32, jq.rr, lane);
+    warp_tri_jobs(M.acc, M.span, M.npix, jq.q + jq.n, 32, jq.rr, lane);
   }
 }
 
 __device__ __forceinline__ void jq_drain(const MapDev &M, JobQueue &jq, int lane) {
-  if (jq.n > 0) warp_tri_jobs(M, jq.q, jq.n, jq.rr, lane);
+  if (jq.n > 0) warp_tri_jobs(M.acc, M.span, M.npix, jq.q, jq.n, jq.rr, lane);
   jq.n = 0;
   __syncwarp();
 }

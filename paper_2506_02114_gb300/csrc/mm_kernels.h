@@ -82,7 +82,9 @@ void build_operator_tables(int p, std::vector<double2> &MM, std::vector<double2>
                            std::vector<double2> &LL);
 
 // ---- shooting + mapping (shoot.cu) -----------------------------------------
-cudaError_t launch_shoot_ipm(const MapDev *d_maps, int n_maps, int64_t total_work, bool square,
+// h_single: the map by value when n_maps == 1 (else NULL: maps from d_maps)
+cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n_maps,
+                             int64_t total_work, bool square,
                              unsigned long long *counter, unsigned *err, int grid,
                              cudaStream_t st);
 cudaError_t launch_normalize(const unsigned long long *acc, const unsigned long long *span,

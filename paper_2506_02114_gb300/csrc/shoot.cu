@@ -192,16 +192,18 @@ __device__ __forceinline__ void flush_counters(const MapDev &M, IpmCounters &cnt
 #define MM_SHOOT_MINB 2  // resident 256-thread blocks per SM the register budget targets
 #endif
 
-template <bool SQUARE>
-__global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *__restrict__ maps, int n_maps,
-                                                   int64_t total_work,
-                                                   unsigned long long *work_counter,
-                                                   unsigned *err) {
+// A single map (BATCH = false) arrives by value as a launch parameter, so
+// its fields are read from the constant bank instead of held in registers;
+// a batch reads its maps from the device array `maps`.
+template <bool SQUARE, bool BATCH>
+__global__ void __launch_bounds__(256, MM_SHOOT_MINB)
+    k_shoot_ipm(const MapDev *__restrict__ maps, const MapDev M1, int n_maps, int64_t total_work,
+                unsigned long long *work_counter, unsigned *err) {
   const int lane = threadIdx.x & 31;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
   WarpQueue wq = {ws->quad, 0};
-  JobQueue jq = {ws->big, ws->rows, 0};
+  JobQueue jq = {ws->big, &ws->rows, 0};
   IpmCounters cnt = {0, 0, 0, 0, 0, 0};
   int last_map = -1;
   while (true) {
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
     w = __shfl_sync(0xffffffffu, w, 0);
     if ((int64_t)w >= total_work) break;
     int mi = 0;
-    if (n_maps > 1) {
+    if (BATCH && n_maps > 1) {
       int lo = 0, hi = n_maps - 1;
       while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -221,9 +223,9 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
       }
       mi = lo;
     }
-    const MapDev &M = maps[mi];
+    const MapDev &M = BATCH ? maps[mi] : M1;
     if (mi != last_map) {  // warp-uniform
-      if (last_map >= 0) flush_counters(maps[last_map], cnt, lane);
+      if (last_map >= 0) flush_counters(BATCH ? maps[last_map] : M1, cnt, lane);
       last_map = mi;
     }
     const int64_t local = (int64_t)w - M.work_begin;
@@ -253,9 +255,17 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
       for (int tri = 0; tri < 2; tri++) {
         TriJob job;
         SmallTri se;
-        const int code = cell_col ? ipm_triangle(M, prev, tri ? cur_r : prev_r,
-                                                 tri ? cur : cur_r, ra, cnt, se, job)
-                                  : TRI_DONE;
+        // triangle 0: (v00, v10, v11); triangle 1: (v00, v11, v01)
+        Vtx vb, vc;
+        vb.px = tri ? cur_r.px : prev_r.px;
+        vb.py = tri ? cur_r.py : prev_r.py;
+        vb.fx = tri ? cur_r.fx : prev_r.fx;
+        vb.fy = tri ? cur_r.fy : prev_r.fy;
+        vc.px = tri ? cur.px : cur_r.px;
+        vc.py = tri ? cur.py : cur_r.py;
+        vc.fx = tri ? cur.fx : cur_r.fx;
+        vc.fy = tri ? cur.fy : cur_r.fy;
+        const int code = cell_col ? ipm_triangle(M, prev, vb, vc, ra, cnt, se, job) : TRI_DONE;
         wq_push(M, wq, code == TRI_SMALL, se, lane);
         jq_push(M, jq, code == TRI_BIG, job, lane);
       }
@@ -265,7 +275,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB) k_shoot_ipm(const MapDev *
     wq_drain(M, wq, lane);
     jq_drain(M, jq, lane);
   }
-  if (last_map >= 0) flush_counters(maps[last_map], cnt, lane);
+  if (last_map >= 0) flush_counters(BATCH ? maps[last_map] : M1, cnt, lane);
 }
 
 // mu = (acc + row-prefix(span)) * 2^-32 * (h_x h_y / 2) / delta^2; one block
@@ -348,22 +358,34 @@ __global__ void k_probe(const MapDev *maps, int64_t n, const double *z, double *
 // host launchers
 // ---------------------------------------------------------------------------
 
-cudaError_t launch_shoot_ipm(const MapDev *d_maps, int n_maps, int64_t total_work,
-                             bool square, unsigned long long *counter, unsigned *err, int grid,
-                             cudaStream_t st) {
-  if (total_work <= 0) return cudaSuccess;
+template <bool SQUARE, bool BATCH>
+static cudaError_t launch_shoot_t(const MapDev *d_maps, const MapDev &m1, int n_maps,
+                                  int64_t total_work, unsigned long long *counter, unsigned *err,
+                                  int grid, cudaStream_t st) {
   const int smem = (int)MM_SHOOT_SMEM_BYTES;
-  cudaError_t e;
-  if (square) {
-    e = cudaFuncSetAttribute(k_shoot_ipm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_shoot_ipm<true><<<grid, 256, smem, st>>>(d_maps, n_maps, total_work, counter, err);
-  } else {
-    e = cudaFuncSetAttribute(k_shoot_ipm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_shoot_ipm<false><<<grid, 256, smem, st>>>(d_maps, n_maps, total_work, counter, err);
-  }
+  cudaError_t e = cudaFuncSetAttribute(k_shoot_ipm<SQUARE, BATCH>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_shoot_ipm<SQUARE, BATCH><<<grid, 256, smem, st>>>(d_maps, m1, n_maps, total_work, counter,
+                                                      err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n_maps,
+                             int64_t total_work, bool square, unsigned long long *counter,
+                             unsigned *err, int grid, cudaStream_t st) {
+  if (total_work <= 0) return cudaSuccess;
+  if (n_maps == 1 && h_single) {
+    return square ? launch_shoot_t<true, false>(nullptr, *h_single, 1, total_work, counter, err,
+                                                grid, st)
+                  : launch_shoot_t<false, false>(nullptr, *h_single, 1, total_work, counter,
+                                                 err, grid, st);
+  }
+  const MapDev none{};
+  return square ? launch_shoot_t<true, true>(d_maps, none, n_maps, total_work, counter, err, grid,
+                                             st)
+                : launch_shoot_t<false, true>(d_maps, none, n_maps, total_work, counter, err,
+                                              grid, st);
 }
 
 cudaError_t launch_normalize(const unsigned long long *acc, const unsigned long long *span,
