@@ -50,7 +50,6 @@
 namespace mm {
 
 #define MM_VTX_INVALID INT_MIN
-#define MM_FAR 1.0e30f
 #define MM_FIX_ONE 4294967296ull  // one whole triangle in fixed-point units
 
 __device__ __forceinline__ float rcp_approx_f(float x) {
@@ -115,30 +114,49 @@ __device__ __forceinline__ void run_add(const MapDev &M, RunAcc &a, long long id
 // areas
 // ---------------------------------------------------------------------------
 
-// Signed area of T n {x < X, y < Y} for T = (0,0), d1, d2.
-__device__ __forceinline__ float quad_area(float d1x, float d1y, float d2x, float d2y, float X,
-                                           float Y) {
-  const float vx[3] = {0.f, d1x, d2x}, vy[3] = {0.f, d1y, d2y};
-  float s = 0.f;
-#pragma unroll
-  for (int e = 0; e < 3; e++) {
-    const float px = vx[e], py = vy[e];
-    const float qx = vx[(e + 1) % 3], qy = vy[(e + 1) % 3];
-    const float dx = qx - px, dy = qy - py;
-    const float tx = (X - px) * rcp_approx_f(dx);
-    const float ty = (Y - py) * rcp_approx_f(dy);
-    float t1 = fminf(tx, ty), t2 = fmaxf(tx, ty);
-    t1 = fminf(fmaxf(t1, 0.f), 1.f);
-    t2 = fminf(fmaxf(t2, 0.f), 1.f);
-    const float p0x = fminf(px, X), p0y = fminf(py, Y);
-    const float p1x = fminf(fmaf(t1, dx, px), X), p1y = fminf(fmaf(t1, dy, py), Y);
-    const float p2x = fminf(fmaf(t2, dx, px), X), p2y = fminf(fmaf(t2, dy, py), Y);
-    const float p3x = fminf(qx, X), p3y = fminf(qy, Y);
-    s = fmaf(p0x, p1y, fmaf(-p1x, p0y, s));
-    s = fmaf(p1x, p2y, fmaf(-p2x, p1y, s));
-    s = fmaf(p2x, p3y, fmaf(-p3x, p2y, s));
+// Split of T by one grid line u = L (u = x or y, coordinates u0, u1, u2):
+// the vertex alone on its side cuts off a triangle similar to T, whose
+// share of the area is d^2 / ((u_a - u_l)(u_b - u_l)), d = L - u_l (the
+// two edge parameters at the line, multiplied).  Returns that share and
+// whether the lone vertex lies on the low side u < L.
+__device__ __forceinline__ float lone_vertex_share(float u0, float u1, float u2, float L,
+                                                   bool &lone_low) {
+  const bool b0 = u0 < L, b1 = u1 < L, b2 = u2 < L;
+  lone_low = (b0 + b1 + b2) == 1;
+  float ul = u2, ua = u0, ub = u1;
+  if (b0 == lone_low) {
+    ul = u0;
+    ua = u1;
+    ub = u2;
+  } else if (b1 == lone_low) {
+    ul = u1;
+    ua = u0;
+    ub = u2;
   }
-  return 0.5f * s;
+  const float d = L - ul;
+  return d * d * rcp_approx_f((ua - ul) * (ub - ul));
+}
+
+// Fixed-point share of T on the low side u < L of one grid line it crosses.
+__device__ __forceinline__ unsigned long long low_side_fixed(float u0, float u1, float u2,
+                                                             float L) {
+  bool lone_low;
+  const unsigned long long v = frac_to_fixed(lone_vertex_share(u0, u1, u2, L, lone_low));
+  return lone_low ? v : MM_FIX_ONE - v;
+}
+
+// Contribution of edge P -> Q to the signed area of T n {x < X, y < Y}
+// (Green's theorem on the boundary clamped to the quadrant): the edge's
+// piece below Y, times the mean of min(x - X, 0) over it.  The terms in X
+// itself sum to zero around T and are left out.
+__device__ __forceinline__ float quadrant_edge(float px, float py, float qx, float qy, float X,
+                                               float Y) {
+  const float ys = fminf(py, Y), ye = fminf(qy, Y);
+  const float xY = fmaf(Y - py, (qx - px) * rcp_approx_f(qy - py), px);  // x on the edge at Y
+  const float xs = py <= Y ? px : xY, xe = qy <= Y ? qx : xY;
+  const float a = fminf(xs, xe) - X, b = fmaxf(xs, xe) - X;
+  const float m = b <= 0.f ? 0.5f * (a + b) : (a >= 0.f ? 0.f : -0.5f * a * a * rcp_approx_f(b - a));
+  return ye != ys ? (ye - ys) * m : 0.f;
 }
 
 // ---------------------------------------------------------------------------
@@ -152,26 +170,28 @@ struct __align__(16) SmallTri {
   float x0, y0, d1x, d1y, d2x, d2y;
 };
 
+// A triangle across both grid lines of a 2 x 2 pixel block: the shares left
+// of X and below Y from the lone vertex on each line, the lower-left share
+// from the quadrant integral; the four pixel shares are differences of
+// those in fixed point and add up to exactly one triangle.
 __device__ __forceinline__ void small_tri_apportion(const MapDev &M, const SmallTri &e) {
-  const float xmin = e.x0 + fminf(0.f, fminf(e.d1x, e.d2x));
-  const float xmax = e.x0 + fmaxf(0.f, fmaxf(e.d1x, e.d2x));
-  const float ymin = e.y0 + fminf(0.f, fminf(e.d1y, e.d2y));
-  const float ymax = e.y0 + fmaxf(0.f, fmaxf(e.d1y, e.d2y));
-  const int c0 = (int)floorf(xmin), c1 = (int)floorf(xmax);
-  const int r0 = (int)floorf(ymin), r1 = (int)floorf(ymax);
-  // dividing lines relative to the first vertex (MM_FAR when not crossed)
-  const float X = (c1 > c0) ? (float)(c0 + 1) - e.x0 : MM_FAR;
-  const float Y = (r1 > r0) ? (float)(r0 + 1) - e.y0 : MM_FAR;
-  const float A = 0.5f * (e.d1x * e.d2y - e.d2x * e.d1y);
-  const float L = quad_area(e.d1x, e.d1y, e.d2x, e.d2y, X, MM_FAR);
-  const float B = quad_area(e.d1x, e.d1y, e.d2x, e.d2y, MM_FAR, Y);
-  const float LB = quad_area(e.d1x, e.d1y, e.d2x, e.d2y, X, Y);
-  const float inv = 1.0f / A;
+  const int c0 = (int)floorf(e.x0 + fminf(0.f, fminf(e.d1x, e.d2x)));
+  const int r0 = (int)floorf(e.y0 + fminf(0.f, fminf(e.d1y, e.d2y)));
+  // the grid lines, relative to the first vertex
+  const float X = (float)(c0 + 1) - e.x0, Y = (float)(r0 + 1) - e.y0;
+  const long long vL = (long long)low_side_fixed(0.f, e.d1x, e.d2x, X);
+  const long long vB = (long long)low_side_fixed(0.f, e.d1y, e.d2y, Y);
+  const float lb = quadrant_edge(0.f, 0.f, e.d1x, e.d1y, X, Y) +
+                   quadrant_edge(e.d1x, e.d1y, e.d2x, e.d2y, X, Y) +
+                   quadrant_edge(e.d2x, e.d2y, 0.f, 0.f, X, Y);
+  const float A2 = e.d1x * e.d2y - e.d2x * e.d1y;  // twice the signed area
+  const long long vLB = (long long)frac_to_fixed(2.f * lb * rcp_approx_f(A2));
+  const long long one = (long long)MM_FIX_ONE;
   const long long gx = (long long)e.ox + c0, gy = (long long)e.oy + r0;
-  deposit(M, gx, gy, frac_to_fixed(LB * inv));
-  if (r1 > r0) deposit(M, gx, gy + 1, frac_to_fixed((L - LB) * inv));
-  if (c1 > c0) deposit(M, gx + 1, gy, frac_to_fixed((B - LB) * inv));
-  if (c1 > c0 && r1 > r0) deposit(M, gx + 1, gy + 1, frac_to_fixed((A - L - B + LB) * inv));
+  deposit(M, gx, gy, (unsigned long long)vLB);
+  deposit(M, gx, gy + 1, (unsigned long long)max(vL - vLB, 0ll));
+  deposit(M, gx + 1, gy, (unsigned long long)max(vB - vLB, 0ll));
+  deposit(M, gx + 1, gy + 1, (unsigned long long)max(one - vL - vB + vLB, 0ll));
 }
 
 // Per-warp queue of SmallTri in shared memory (capacity 64 >= 31 + 31 + 2).
@@ -296,22 +316,8 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     // in fixed point, so the pair sums to exactly one triangle.
     const int o = cy1 - cy0;  // 0: vertical line, 1: horizontal line
     const float L = (float)(o ? cy0 : cx0) + 1.f;
-    const float u0 = t[o], u1 = t[2 + o], u2 = t[4 + o];
-    const bool b0 = u0 < L, b1 = u1 < L, b2 = u2 < L;
-    const bool lone_low = (b0 + b1 + b2) == 1;
-    float ul = u2, ua = u0, ub = u1;
-    if (b0 == lone_low) {
-      ul = u0;
-      ua = u1;
-      ub = u2;
-    } else if (b1 == lone_low) {
-      ul = u1;
-      ua = u0;
-      ub = u2;
-    }
-    const float d = L - ul;
-    const unsigned long long vl = frac_to_fixed(d * d * rcp_approx_f((ua - ul) * (ub - ul)));
-    const unsigned long long vlow = lone_low ? vl : MM_FIX_ONE - vl;
+    const unsigned long long vlow = low_side_fixed(t[o], t[2 + o], t[4 + o], L);
+    const bool b0 = t[o] < L;  // vertex a on the low side
     // the pixel holding vertex a goes through the run accumulator
     const long long glx = (long long)ox + cx0, gly = (long long)oy + cy0;  // low pixel
     const long long gax = b0 ? glx : glx + 1 - o, gay = b0 ? gly : gly + o;
@@ -471,6 +477,26 @@ struct RowRecs {
   int gx0[32], gy[32], fa[32], fb[32];
 };
 
+// Partially covered pixel number `task` of a round's rows (all 32 lanes call).
+__device__ __forceinline__ void pixel_task(const MapAcc &M, const RowRecs *rr, int pincl,
+                                           int pexcl, int task, int ptotal) {
+  const int j = scan_owner(pincl, task);
+  const int jst = __shfl_sync(0xffffffffu, pexcl, j);
+  if (task < ptotal) {
+    const int fa = rr->fa[j], fb = rr->fb[j];
+    int c = task - jst;
+    if (fa <= fb && c >= fa) c += fb - fa + 1;
+    const float cl = (float)c;
+    float sh = 0.f;
+#pragma unroll
+    for (int e = 0; e < 3; e++)
+      sh = fmaf(rr->h[e][j], piece_mean(rr->a[e][j] - cl, rr->b[e][j] - cl), sh);
+    // the row and its columns lie in the map (clamped when the row was set up)
+    const unsigned long long v = frac_to_fixed(sh);
+    if (v) atomicAdd(&M.acc[(long long)rr->gy[j] * M.npix + rr->gx0[j] + c], v);
+  }
+}
+
 // The nb (<= 32) triangles q[0..nb) (warp shared memory) spanning more than
 // 2 x 2 pixels.  Their pixel rows within the map are dealt out to the lanes,
 // 32 at a time; a row adds 1/|area| to its fully covered run through the
@@ -537,26 +563,14 @@ static __device__ __noinline__ void warp_tri_jobs(unsigned long long *acc,
       }
     }
     __syncwarp();
-    // the partially covered pixels of these 32 rows
+    // the partially covered pixels of these 32 rows, two per lane at a time
+    // (two independent owner searches and area chains in flight)
     const int pincl = warp_incl_scan(np, lane);
     const int ptotal = __shfl_sync(0xffffffffu, pincl, 31);
-    for (int pbase = 0; pbase < ptotal; pbase += 32) {
-      const int ptask = pbase + lane;
-      const int j = scan_owner(pincl, ptask);
-      const int jst = __shfl_sync(0xffffffffu, pincl - np, j);
-      if (ptask < ptotal) {
-        const int fa = rr->fa[j], fb = rr->fb[j];
-        int c = ptask - jst;
-        if (fa <= fb && c >= fa) c += fb - fa + 1;
-        const float cl = (float)c;
-        float sh = 0.f;
-#pragma unroll
-        for (int e = 0; e < 3; e++)
-          sh = fmaf(rr->h[e][j], piece_mean(rr->a[e][j] - cl, rr->b[e][j] - cl), sh);
-        // the row and its columns lie in the map (clamped above)
-        const unsigned long long v = frac_to_fixed(sh);
-        if (v) atomicAdd(&M.acc[(long long)rr->gy[j] * M.npix + rr->gx0[j] + c], v);
-      }
+    const int pexcl = pincl - np;
+    for (int pbase = 0; pbase < ptotal; pbase += 64) {
+      pixel_task(M, rr, pincl, pexcl, pbase + lane, ptotal);
+      pixel_task(M, rr, pincl, pexcl, pbase + 32 + lane, ptotal);
     }
     __syncwarp();
   }
