@@ -73,11 +73,15 @@ typedef struct {
                                resident warp >= 16 items */
   int32_t sub_levels;       /* FMM mode: each leaf's local expansion is re-centred
                                exactly on its 4^s sub-cells (s levels below the
-                               leaf) and evaluated to the fewest terms whose
+                               leaf); a sub-cell sums directly only the leaf's
+                               near stars within its 5 x 5 block of sub-cells and
+                               takes the others into its expansion (P2L); the
+                               expansion is evaluated to the fewest terms whose
                                truncation bound matches order p at the leaf
-                               centre (App. C error model).  -1: none; 0: the
-                               default (2); 1 or 2: s.  Capped so that leaves
-                               plus sub-cells stay within 21 tree levels. */
+                               centre (App. C error model).  -1: none (the
+                               leaf-level scheme); 0: the default (2); 1 or 2: s.
+                               Capped so that leaves plus sub-cells stay within
+                               21 tree levels. */
   int64_t col_begin;        /* shoot only cell columns [col_begin, col_end) of */
   int64_t col_end;          /*   the ray grid; both 0 -> every column */
 } mm_options;

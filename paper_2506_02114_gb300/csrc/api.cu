@@ -380,12 +380,16 @@ static mm_status run_tree(mm_map *h, cudaStream_t st, bool plan) {
 // far-field stars of a leaf of half-length L lie outside its 3 x 3 block
 // (L-inf distance >= 3L from the centre), so truncating the expansion about
 // the leaf centre at order p errs by ~ (sqrt(2) L / 3L)^p at a corner.  About
-// the centre of a sub-cell of half-length L/2^s the ratio is
-// sqrt(2) 2^-s / (2 + 2^-s); keep the fewest terms that do as well.
+// the centre of a sub-cell of half-length L/2^s the far field's ratio is
+// sqrt(2) 2^-s / (2 + 2^-s), and the near stars moved into the sub-cell's
+// expansion (outside its (2K+1)^2 block of sub-cells) add the ratio
+// sqrt(2) / (2K+1); keep the fewest terms that do as well as order p at the
+// leaf centre for the larger of the two.
 static int eval_terms(int p, int s) {
   if (s <= 0 || p <= 2) return p;
   const double r0 = std::sqrt(2.0) / 3.0;
-  const double q = std::ldexp(1.0, -s), rs = std::sqrt(2.0) * q / (2.0 + q);
+  const double q = std::ldexp(1.0, -s);
+  const double rs = std::max(std::sqrt(2.0) * q / (2.0 + q), std::sqrt(2.0) / (2 * MM_NEAR_K + 1));
   const int pe = (int)std::ceil(p * std::log(r0) / std::log(rs) - 1e-9);
   return std::max(2, std::min(p, pe));
 }
@@ -459,8 +463,8 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
     CK(cudaStreamSynchronize(st));
     CK(h->mp.ensure((size_t)nn * (h->p + 1)));
     CK(h->loc.ensure((size_t)nn * (h->p + 1)));
-    CK(h->near_cnt.ensure(h->n_active));
-    CK(h->near_off.ensure(h->n_active));
+    CK(h->near_cnt.ensure(h->n_active << (2 * h->sub)));
+    CK(h->near_off.ensure(h->n_active << (2 * h->sub)));
     CK(h->err.ensure(1));
   }
   const int p = h->p, P1 = p + 1;
@@ -476,25 +480,7 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
     LCH(launch_local(T, l, h->level_cnt[l], p, h->node_act.p, h->MLop.p, h->LLop.p, h->mp.p,
                     h->loc.p, h->err.p, st));
 
-  // near-field lists and leaf records
-  LCH(launch_near_count(T, h->n_active, h->active_list.p, h->near_cnt.p, h->err.p, st));
-  CKS(cub_call(h, plan, [&](void *tmp, size_t &bytes) {
-    return cub::DeviceScan::ExclusiveSum(tmp, bytes, h->near_cnt.p, h->near_off.p,
-                                         (int)h->n_active, st);
-  }));
-  if (plan) {
-    cudaError_t e;
-    int32_t a = read_scalar(h->near_off.p + (h->n_active - 1), st, e);
-    CK(e);
-    int32_t b = read_scalar(h->near_cnt.p + (h->n_active - 1), st, e);
-    CK(e);
-    h->n_near = (int64_t)a + b;
-    const int64_t n_rec = h->n_active << (2 * h->sub);
-    CK(h->leaf.ensure(n_rec));
-    CK(h->near_pos.ensure(h->n_near));
-    CK(h->near_m.ensure(h->n_near));
-    CK(h->coef.ensure((size_t)n_rec * coef_stride(h->p_eval)));
-  }
+  // near-field lists and leaf records, per sub-cell record
   FmmConst C;
   C.p = p;
   C.p_eval = h->p_eval;
@@ -509,6 +495,24 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
   C.lox = P.center_y[0] - P.half_length;
   C.loy = P.center_y[1] - P.half_length;
   C.delta = P.delta;
+  const int64_t n_rec = h->n_active << (2 * h->sub);
+  LCH(launch_near_count(T, C, h->n_active, h->active_list.p, h->near_cnt.p, h->err.p, st));
+  CKS(cub_call(h, plan, [&](void *tmp, size_t &bytes) {
+    return cub::DeviceScan::ExclusiveSum(tmp, bytes, h->near_cnt.p, h->near_off.p, (int)n_rec,
+                                         st);
+  }));
+  if (plan) {
+    cudaError_t e;
+    int32_t a = read_scalar(h->near_off.p + (n_rec - 1), st, e);
+    CK(e);
+    int32_t b = read_scalar(h->near_cnt.p + (n_rec - 1), st, e);
+    CK(e);
+    h->n_near = (int64_t)a + b;
+    CK(h->leaf.ensure(n_rec));
+    CK(h->near_pos.ensure(h->n_near));
+    CK(h->near_m.ensure(h->n_near));
+    CK(h->coef.ensure((size_t)n_rec * coef_stride(h->p_eval)));
+  }
   LCH(launch_leaf_finalize(T, C, h->n_active, h->active_list.p, h->near_off.p, h->near_cnt.p,
                           h->loc.p, h->leaf.p, h->near_pos.p, h->near_m.p, h->coef.p,
                           h->err.p, st));

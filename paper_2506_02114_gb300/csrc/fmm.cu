@@ -234,46 +234,80 @@ __device__ __forceinline__ int for_each_near_range(const TreeDev &T, int64_t nod
   return 0;
 }
 
-__global__ void k_near_count(TreeDev T, int64_t n_active, const int32_t *active_list,
-                             int32_t *near_cnt, unsigned *err) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_active) return;
-  int64_t total = 0;
-  for_each_near_range(T, active_list[t], [&](int64_t b, int64_t e) { total += e - b; }, err);
-  near_cnt[t] = (int32_t)total;
+// Sub-cell q of active leaf t (records are numbered g = 4^s t + q, q
+// row-major with y major): its centre and half-length.
+__device__ __forceinline__ void sub_cell_geom(const TreeDev &T, const FmmConst &C,
+                                              const int32_t *active_list, int64_t g,
+                                              int64_t &node, double &zx, double &zy,
+                                              double &L, double &cx, double &cy, double &Lq) {
+  const int ns = 1 << C.sub, NS = ns * ns;
+  const int64_t t = g / NS;
+  const int q = (int)(g % NS), qx = q & (ns - 1), qy = q >> C.sub;
+  node = active_list[t];
+  int level, nx, ny;
+  node_geom(T, node, level, nx, ny, zx, zy, L);
+  Lq = L / ns;
+  cx = zx + (double)(2 * qx + 1 - ns) * Lq;
+  cy = zy + (double)(2 * qy + 1 - ns) * Lq;
 }
 
-// One thread per (active leaf t, sub-cell q).  The leaf's local expansion
-// psi = sum_l c_l zeta^l, zeta = (z - z_c)/L, is re-centred exactly on the
-// sub-cell centre z_q (an L2L translation to a descendant of the leaf, which
-// receives no further M2L terms: its far field is the leaf's):
-//   d_n = (L_q/L)^n sum_{l>=n} C(l, n) c_l u^(l-n),  u = (z_q - z_c)/L,
-// and kept to n <= p_eval.  The thread for q = 0 also writes the leaf's
-// near-field list, shared by all its sub-cells.  A record's coefficients
+// Whether a star of the leaf's near field stays in the sub-cell's direct
+// sum: without sub-cells every one does; with them, those within the
+// (2 MM_NEAR_K + 1)^2 block of sub-cells around it (L-inf distance below
+// (2 MM_NEAR_K + 1) L_q from its centre).  The others join its local
+// expansion (P2L), which they leave converging at least as fast as the
+// ratio sqrt(2) / (2 MM_NEAR_K + 1).
+__device__ __forceinline__ bool stays_direct(const FmmConst &C, double dx, double dy,
+                                             double Lq) {
+  if (C.sub == 0) return true;
+  const double hw = (2 * MM_NEAR_K + 1) * Lq;
+  return fabs(dx) < hw && fabs(dy) < hw;
+}
+
+// Direct-sum stars per sub-cell record.
+__global__ void k_near_count(TreeDev T, FmmConst C, int64_t n_rec, const int32_t *active_list,
+                             int32_t *near_cnt, unsigned *err) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_rec) return;
+  int64_t node;
+  double zx, zy, L, cx, cy, Lq;
+  sub_cell_geom(T, C, active_list, g, node, zx, zy, L, cx, cy, Lq);
+  int64_t total = 0;
+  for_each_near_range(
+      T, node,
+      [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; i++) total += stays_direct(C, T.sx[i] - cx, T.sy[i] - cy, Lq);
+      },
+      err);
+  near_cnt[g] = (int32_t)total;
+}
+
+// One thread per sub-cell record g (active leaf t, sub-cell q).  The leaf's
+// local expansion psi = sum_l c_l zeta^l, zeta = (z - z_c)/L, is re-centred
+// exactly on the sub-cell centre z_q (an L2L translation to a descendant of
+// the leaf, which receives no further M2L terms: its far field is the
+// leaf's):
+//   d_n = (L_q/L)^n sum_{l>=n} C(l, n) c_l u^(l-n),  u = (z_q - z_c)/L;
+// the leaf's near-field stars that leave the direct sum (stays_direct) add
+// their own expansion about z_q (P2L): m log(z - z_i) contributes
+//   d_n += -m / (n w^n),  w = (z_i - z_q)/L_q,  n >= 1,
+// and the result is kept to n <= p_eval.  A record's coefficients
 // e_n = n d_n / (L_q delta), n = 2..p_eval, take coef_stride(p_eval) slots
-// (an even count, zero-padded) so the kernel loads them in pairs.
-__global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_active,
+// (an even count, zero-padded) so the kernel loads them in pairs; its
+// direct stars are stored in its own grid frame.
+__global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
                                 const int32_t *active_list, const int32_t *near_off,
                                 const int32_t *near_cnt, const double2 *__restrict__ loc,
                                 LeafRec *leaf, NearPos *near_pos, float *near_m, float2 *coef,
                                 unsigned *err) {
-  const int ns = 1 << C.sub, NS = ns * ns;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n_active * NS) return;
-  const int64_t t = g / NS;
-  const int q = (int)(g % NS), qx = q & (ns - 1), qy = q >> C.sub;
-  const int64_t node = active_list[t];
-  int level, nx, ny;
-  double zx, zy, L;
-  node_geom(T, node, level, nx, ny, zx, zy, L);
-  const int p = C.p, P1 = p + 1, pe = C.p_eval, cs = coef_stride(pe);
+  if (g >= n_rec) return;
+  int64_t node;
+  double zx, zy, L, cx, cy, Lq;
+  sub_cell_geom(T, C, active_list, g, node, zx, zy, L, cx, cy, Lq);
+  const int p = C.p, P1 = p + 1, pe = min(C.p_eval, MM_PMAX), cs = coef_stride(pe);
 
-  // grid vertex nearest the leaf centre: frame of the near list
-  const double li = rint((zx - C.x0) / C.hx), lj = rint((zy - C.y0) / C.hy);
-  // the sub-cell and the grid vertex nearest its centre
-  const double ux = (double)(2 * qx + 1 - ns) / ns, uy = (double)(2 * qy + 1 - ns) / ns;
-  const double Lq = L / ns;
-  const double cx = zx + ux * L, cy = zy + uy * L;
+  // the grid vertex nearest the sub-cell centre
   const double gi = rint((cx - C.x0) / C.hx), gj = rint((cy - C.y0) / C.hy);
   const double xr = C.x0 + gi * C.hx, yr = C.y0 + gj * C.hy;
   LeafRec R;
@@ -281,37 +315,75 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_active,
   R.j_ref = (int32_t)gj;
   R.fcx = (float)((cx - xr) / C.hx);
   R.fcy = (float)((cy - yr) / C.hy);
-  R.offi = (float)(gi - li);
-  R.offj = (float)(gj - lj);
+  R.pad0 = R.pad1 = 0;
 
-  // d_1 and the kept coefficients d_2..d_pe of the re-centred expansion
+  // re-centred leaf expansion, d_1 .. d_pe
+  double2 d[MM_PMAX + 1];
   const double2 *c = loc + node * P1;
-  const double r = 1.0 / ns;
-  const double s = 1.0 / (Lq * C.delta);
+  const double ux = (cx - zx) / L, uy = (cy - zy) / L, r = Lq / L;
   double rn = 1.0;
-  double2 d1 = make_double2(0.0, 0.0);
-  for (int n = 1; n <= pe && n <= p; n++) {
+  for (int n = 1; n <= pe; n++) {
     rn *= r;
     double sx = 0.0, sy = 0.0, px = 1.0, py = 0.0, binom = 1.0;  // u^(l-n), C(l, n)
     for (int l = n; l <= p; l++) {
       const double2 cl = c[l];
-      const double tx = cl.x * px - cl.y * py, ty = cl.x * py + cl.y * px;
-      sx += binom * tx;
-      sy += binom * ty;
+      sx += binom * (cl.x * px - cl.y * py);
+      sy += binom * (cl.x * py + cl.y * px);
       const double npx = px * ux - py * uy;
       py = px * uy + py * ux;
       px = npx;
       binom = binom * (double)(l + 1) / (double)(l + 1 - n);
     }
-    const double2 dn = make_double2(sx * rn, sy * rn);
-    if (n == 1)
-      d1 = dn;
-    else
-      coef[g * cs + (n - 2)] = make_float2((float)(n * dn.x * s), (float)(n * dn.y * s));
+    d[n] = make_double2(sx * rn, sy * rn);
   }
-  for (int k = pe - 1; k < cs; k++) coef[g * cs + k] = make_float2(0.f, 0.f);
+
+  // near-field stars: direct (in this record's frame) or into the expansion;
+  // the direct ones never exceed the slots k_near_count reserved
+  int64_t k = near_off[g];
+  const int64_t kend = k + near_cnt[g];
+  for_each_near_range(
+      T, node,
+      [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; i++) {
+          const double dxs = T.sx[i] - cx, dys = T.sy[i] - cy;
+          if (stays_direct(C, dxs, dys, Lq) && k < kend) {
+            const double sxg = (T.sx[i] - xr) / C.hx, syg = (T.sy[i] - yr) / C.hy;
+            const double Kx = rint(sxg), Ky = rint(syg);
+            NearPos np;
+            np.Kx = (float)Kx;
+            np.fx = (float)(sxg - Kx);
+            np.Ky = (float)Ky;
+            np.fy = (float)(syg - Ky);
+            near_pos[k] = np;
+            near_m[k] = (float)T.sm[i];
+            k++;
+          } else {
+            // 1/w = L_q / (z_i - z_q)
+            const double den = dxs * dxs + dys * dys;
+            const double ix = Lq * dxs / den, iy = -Lq * dys / den;
+            const double m = T.sm[i];
+            double tx = ix, ty = iy;  // w^-n
+            for (int n = 1; n <= pe; n++) {
+              d[n].x -= m * tx / n;
+              d[n].y -= m * ty / n;
+              const double ntx = tx * ix - ty * iy;
+              ty = tx * iy + ty * ix;
+              tx = ntx;
+            }
+          }
+        }
+      },
+      err);
+  R.near_off = near_off[g];
+  R.near_cnt = (int32_t)(k - R.near_off);
+
+  const double s = 1.0 / (Lq * C.delta);
+  for (int n = 2; n <= pe; n++)
+    coef[g * cs + (n - 2)] = make_float2((float)(n * d[n].x * s), (float)(n * d[n].y * s));
+  for (int kk = pe - 1; kk < cs; kk++) coef[g * cs + kk] = make_float2(0.f, 0.f);
 
   // FP64 image of the sub-cell centre: macro model + sheet - far field there
+  const double2 d1 = pe >= 1 ? d[1] : make_double2(0.0, 0.0);
   const double ak = 1.0 - C.kappa + C.kappa_star;
   const double Wx = (ak + C.gamma) * cx - d1.x / Lq;
   const double Wy = (ak - C.gamma) * cy + d1.y / Lq;  // - conj(d1/L_q)
@@ -326,33 +398,9 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_active,
   R.Vf = (float)(V - Vi);
   R.zsx = (float)(C.hx / Lq);
   R.zsy = (float)(C.hy / Lq);
-  R.near_off = near_off[t];
-  R.near_cnt = near_cnt[t];
   R.coef_off = (int32_t)(g * cs);
   R.node = (int32_t)node;
   leaf[g] = R;
-
-  if (q != 0) return;
-  // near-field stars in the frame of the vertex nearest the leaf centre
-  const double xl = C.x0 + li * C.hx, yl = C.y0 + lj * C.hy;
-  int64_t k = R.near_off;
-  for_each_near_range(
-      T, node,
-      [&](int64_t b, int64_t e) {
-        for (int64_t i = b; i < e; i++) {
-          const double sxg = (T.sx[i] - xl) / C.hx, syg = (T.sy[i] - yl) / C.hy;
-          const double Kx = rint(sxg), Ky = rint(syg);
-          NearPos np;
-          np.Kx = (float)Kx;
-          np.fx = (float)(sxg - Kx);
-          np.Ky = (float)Ky;
-          np.fy = (float)(syg - Ky);
-          near_pos[k] = np;
-          near_m[k] = (float)T.sm[i];
-          k++;
-        }
-      },
-      err);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,11 +510,12 @@ cudaError_t launch_local(const TreeDev &T, int level, int64_t n, int p, const in
   return cudaGetLastError();
 }
 
-cudaError_t launch_near_count(const TreeDev &T, int64_t n_active, const int32_t *active_list,
-                              int32_t *near_cnt, unsigned *err, cudaStream_t st) {
+cudaError_t launch_near_count(const TreeDev &T, const FmmConst &C, int64_t n_active,
+                              const int32_t *active_list, int32_t *near_cnt, unsigned *err,
+                              cudaStream_t st) {
   if (n_active <= 0) return cudaSuccess;
-  k_near_count<<<blocks_for(n_active, 128), 128, 0, st>>>(T, n_active, active_list, near_cnt,
-                                                         err);
+  const int64_t n = n_active << (2 * C.sub);
+  k_near_count<<<blocks_for(n, 128), 128, 0, st>>>(T, C, n, active_list, near_cnt, err);
   return cudaGetLastError();
 }
 
@@ -477,7 +526,7 @@ cudaError_t launch_leaf_finalize(const TreeDev &T, const FmmConst &C, int64_t n_
                                  cudaStream_t st) {
   if (n_active <= 0) return cudaSuccess;
   const int64_t n = n_active << (2 * C.sub);
-  k_leaf_finalize<<<blocks_for(n, 64), 64, 0, st>>>(T, C, n_active, active_list, near_off,
+  k_leaf_finalize<<<blocks_for(n, 64), 64, 0, st>>>(T, C, n, active_list, near_off,
                                                     near_cnt, loc, leaf, near_pos, near_m, coef,
                                                     err);
   return cudaGetLastError();

@@ -563,15 +563,12 @@ static __device__ __noinline__ void warp_tri_jobs(unsigned long long *acc,
       }
     }
     __syncwarp();
-    // the partially covered pixels of these 32 rows, two per lane at a time
-    // (two independent owner searches and area chains in flight)
+    // the partially covered pixels of these 32 rows, one per lane at a time
     const int pincl = warp_incl_scan(np, lane);
     const int ptotal = __shfl_sync(0xffffffffu, pincl, 31);
     const int pexcl = pincl - np;
-    for (int pbase = 0; pbase < ptotal; pbase += 64) {
+    for (int pbase = 0; pbase < ptotal; pbase += 32)
       pixel_task(M, rr, pincl, pexcl, pbase + lane, ptotal);
-      pixel_task(M, rr, pincl, pexcl, pbase + 32 + lane, ptotal);
-    }
     __syncwarp();
   }
 }

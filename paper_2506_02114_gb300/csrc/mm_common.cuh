@@ -13,6 +13,9 @@
 #define MM_PMAX 64            // largest expansion order accepted by the ABI
 #define MM_SUB_MAX 2          // largest sub-cell level count (16 sub-cells per leaf)
 #define MM_SUB_DEFAULT 2      // sub-cell levels when the options leave it to the library
+#define MM_NEAR_K 2           // with sub-cells, a sub-cell sums directly the leaf's near
+                              // stars in its (2K+1)^2 block of sub-cells; the rest go
+                              // into its local expansion
 #define MM_STRIP 31           // cell columns per warp work item (32 vertex columns)
 #define MM_MED_PIXELS 64      // bounding box (map pixels) up to which a larger
                               // triangle is counted as medium in the statistics
@@ -37,15 +40,14 @@ struct __align__(16) LeafRec {
   int32_t Ui, Vi;             // integer part of the centre's image in pixels
   float Uf, Vf;               // fractional part (FP64-accurate)
   float zsx, zsy;             // h_x / L_s, h_y / L_s : grid units -> zeta units
-  int32_t near_off, near_cnt; // the leaf's near-field stars in near_pos/near_m
+  int32_t near_off, near_cnt; // the sub-cell's direct-sum stars in near_pos/near_m
   int32_t coef_off;           // first of coef_stride(p_eval) far-field coefficient slots
   int32_t node;               // tree node id of the leaf
-  float offi, offj;           // (i_ref, j_ref) minus the near list's reference vertex
+  int32_t pad0, pad1;
 };
 
-// Near-field star in the leaf's grid frame: grid position relative to the
-// grid vertex closest to the leaf centre = (Kx + fx, Ky + fy), K
-// integer-valued, |f| <= 0.5.
+// Direct-sum star in its record's grid frame: grid position relative to
+// (i_ref, j_ref) = (Kx + fx, Ky + fy), K integer-valued, |f| <= 0.5.
 struct __align__(16) NearPos {
   float Kx, fx, Ky, fy;
 };

@@ -71,8 +71,9 @@ cudaError_t launch_m2m(const TreeDev &T, int level, int64_t n, int p, const doub
 cudaError_t launch_local(const TreeDev &T, int level, int64_t n, int p, const int32_t *node_act,
                          const double2 *MLop, const double2 *LLop, const double2 *mp,
                          double2 *loc, unsigned *err, cudaStream_t st);
-cudaError_t launch_near_count(const TreeDev &T, int64_t n_active, const int32_t *active_list,
-                              int32_t *near_cnt, unsigned *err, cudaStream_t st);
+cudaError_t launch_near_count(const TreeDev &T, const FmmConst &C, int64_t n_active,
+                              const int32_t *active_list, int32_t *near_cnt, unsigned *err,
+                              cudaStream_t st);
 cudaError_t launch_leaf_finalize(const TreeDev &T, const FmmConst &C, int64_t n_active,
                                  const int32_t *active_list, const int32_t *near_off,
                                  const int32_t *near_cnt,

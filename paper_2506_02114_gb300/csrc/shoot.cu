@@ -58,14 +58,11 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
   const float zsx = __int_as_float(q2.x), zsy = __int_as_float(q2.y);
   const int near_off = q2.z, near_cnt = (leaf < 0) ? 0 : q2.w;
   const int coef_off = q3.x;
-  const float offi = __int_as_float(q3.z), offj = __int_as_float(q3.w);
 
   // vertex position relative to the reference vertex, in grid units (exact
   // integers), and relative to the leaf centre
   const float fi = (float)(int)(i - i_ref), fj = (float)(int)(j - j_ref);
   float gx = fi - fcx, gy = fj - fcy;
-  // the same vertex in the near list's frame (integers, exact)
-  const float ni = fi + offi, nj = fj + offj;
   if (FRAC) {
     gx += ti;
     gy += tj;
@@ -83,8 +80,8 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
     const float4 s0 = a0 ? __ldg(np_ + k) : make_float4(0.f, 1.f, 0.f, 0.f);
     const float4 s1 = a1 ? __ldg(np_ + k + 1) : make_float4(0.f, 1.f, 0.f, 0.f);
     const float m0 = a0 ? __ldg(nm_ + k) : 0.f, m1 = a1 ? __ldg(nm_ + k + 1) : 0.f;
-    float dx0 = (ni - s0.x) - s0.y, dy0 = (nj - s0.z) - s0.w;
-    float dx1 = (ni - s1.x) - s1.y, dy1 = (nj - s1.z) - s1.w;
+    float dx0 = (fi - s0.x) - s0.y, dy0 = (fj - s0.z) - s0.w;
+    float dx1 = (fi - s1.x) - s1.y, dy1 = (fj - s1.z) - s1.w;
     if (FRAC) {
       dx0 += ti;
       dy0 += tj;
@@ -102,7 +99,7 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
   if (k < maxcnt && k < near_cnt) {
     const float4 s0 = __ldg(np_ + k);
     const float m0 = __ldg(nm_ + k);
-    float dx0 = (ni - s0.x) - s0.y, dy0 = (nj - s0.z) - s0.w;
+    float dx0 = (fi - s0.x) - s0.y, dy0 = (fj - s0.z) - s0.w;
     if (FRAC) {
       dx0 += ti;
       dy0 += tj;
