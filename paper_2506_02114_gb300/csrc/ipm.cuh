@@ -442,18 +442,19 @@ __device__ __forceinline__ void tri_row_extent(const TriJob &J, int r, int &c0, 
   }
 }
 
-// Owner lane of task `task`: the first lane whose inclusive count exceeds it.
-__device__ __forceinline__ int scan_owner(int incl, int task) {
-  int lo = 0, hi = 31;
-#pragma unroll
-  for (int it = 0; it < 5; it++) {
-    const int mid = (lo + hi) >> 1;
-    if (__shfl_sync(0xffffffffu, incl, mid) > task)
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
-  return lo;
+// Dealing tasks from a warp's lanes: lane j owns n_j tasks, numbered
+// [ex_j, ex_j + n_j) in lane order (ex the exclusive scan), and the lanes
+// with n_j > 0 are ranked by slot = their rank among them.  For the 32 tasks
+// [base, base + 32), the owner of task base + l has slot
+//   i0 + |{starts ex_j in (base, base + l]}|,  i0 = |{n_j > 0, ex_j <= base}| - 1,
+// found with one ballot, one OR-reduction of start bits and a popcount:
+// no chain of shuffles.
+__device__ __forceinline__ int deal_owner_slot(int n, int ex, int base, int lane) {
+  const int i0 = __popc(__ballot_sync(0xffffffffu, n > 0 && ex <= base)) - 1;
+  const int d = ex - base;
+  const unsigned bit = (n > 0 && d > 0 && d < 32) ? (1u << d) : 0u;
+  const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
+  return i0 + __popc(starts & ((2u << lane) - 1u));
 }
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
@@ -465,7 +466,8 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
   return v;
 }
 
-// The pixel rows of one round of a larger-triangle batch, one per lane,
+// The pixel rows of one round of a larger-triangle batch, by slot (rank
+// among the rows with partially covered pixels),
 // shared by the lanes that measure their partially covered pixels: for each
 // edge its piece in the row band, x relative to column c0, with height
 // times 2/area (so the weighted sum of piece means is the pixel's share);
@@ -475,25 +477,26 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 struct RowRecs {
   float a[3][32], b[3][32], h[3][32];
   int gx0[32], gy[32], fa[32], fb[32];
+  int st[32];                  // first partial-pixel task of the row
+  int tk[32], trl[32], tex[32];  // triangles with rows: lane, first row, first row task
 };
 
-// Partially covered pixel number `task` of a round's rows (all 32 lanes call).
-__device__ __forceinline__ void pixel_task(const MapAcc &M, const RowRecs *rr, int pincl,
-                                           int pexcl, int task, int ptotal) {
-  const int j = scan_owner(pincl, task);
-  const int jst = __shfl_sync(0xffffffffu, pexcl, j);
+// Partially covered pixel number `task` of a round's rows, owned by the row
+// in slot o.
+__device__ __forceinline__ void pixel_task(const MapAcc &M, const RowRecs *rr, int o, int task,
+                                           int ptotal) {
   if (task < ptotal) {
-    const int fa = rr->fa[j], fb = rr->fb[j];
-    int c = task - jst;
+    const int fa = rr->fa[o], fb = rr->fb[o];
+    int c = task - rr->st[o];
     if (fa <= fb && c >= fa) c += fb - fa + 1;
     const float cl = (float)c;
     float sh = 0.f;
 #pragma unroll
     for (int e = 0; e < 3; e++)
-      sh = fmaf(rr->h[e][j], piece_mean(rr->a[e][j] - cl, rr->b[e][j] - cl), sh);
+      sh = fmaf(rr->h[e][o], piece_mean(rr->a[e][o] - cl, rr->b[e][o] - cl), sh);
     // the row and its columns lie in the map (clamped when the row was set up)
     const unsigned long long v = frac_to_fixed(sh);
-    if (v) atomicAdd(&M.acc[(long long)rr->gy[j] * M.npix + rr->gx0[j] + c], v);
+    if (v) atomicAdd(&M.acc[(long long)rr->gy[o] * M.npix + rr->gx0[o] + c], v);
   }
 }
 
@@ -520,15 +523,25 @@ static __device__ __noinline__ void warp_tri_jobs(unsigned long long *acc,
     nrows = r1 >= r0 ? r1 - r0 + 1 : 0;
   }
   const int incl = warp_incl_scan(nrows, lane);
+  const int excl = incl - nrows;
   const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const unsigned with_rows = __ballot_sync(0xffffffffu, nrows > 0);
+  if (nrows > 0) {
+    const int slot = __popc(with_rows & ((1u << lane) - 1u));
+    rr->tk[slot] = lane;
+    rr->trl[slot] = rl;
+    rr->tex[slot] = excl;
+  }
+  __syncwarp();
   for (int base = 0; base < total; base += 32) {
     const int task = base + lane;
-    const int k = scan_owner(incl, task);
-    const int r = __shfl_sync(0xffffffffu, rl, k) + task - __shfl_sync(0xffffffffu, incl - nrows, k);
-    int np = 0;
+    const int o = deal_owner_slot(nrows, excl, base, lane);
+    int np = 0, r = 0, c0 = 0, fa = 1, fb = 0, k = 0;
     if (task < total) {
+      k = rr->tk[o];
+      r = rr->trl[o] + task - rr->tex[o];
       const TriJob &J = q[k];
-      int c0, c1, fa, fb;
+      int c1;
       tri_row_extent(J, r, c0, c1, fa, fb);
       c0 = max(c0, -J.ox);
       c1 = min(c1, M.npix - 1 - J.ox);
@@ -545,32 +558,36 @@ static __device__ __noinline__ void warp_tri_jobs(unsigned long long *acc,
           atomicAdd(&sp[J.ox + fb + 1], 0ull - full);
         }
       }
-      if (np > 0) {
-        const float fc0 = (float)c0, fr = (float)r;
+    }
+    // the partially covered pixels of these 32 rows: records by slot
+    const int pincl = warp_incl_scan(np, lane);
+    const int pexcl = pincl - np;
+    const int ptotal = __shfl_sync(0xffffffffu, pincl, 31);
+    const int slot = __popc(__ballot_sync(0xffffffffu, np > 0) & ((1u << lane) - 1u));
+    __syncwarp();  // the previous round's readers are done with the records
+    if (np > 0) {
+      const TriJob &J = q[k];
+      const float fc0 = (float)c0, fr = (float)r;
 #pragma unroll
-        for (int e = 0; e < 3; e++) {
-          float a, b, h;
-          edge_piece(J.t[2 * e] - fc0, J.t[2 * e + 1] - fr, J.t[(2 * e + 2) % 6] - fc0,
-                     J.t[(2 * e + 3) % 6] - fr, J.k[e], a, b, h);
-          rr->a[e][lane] = a;
-          rr->b[e][lane] = b;
-          rr->h[e][lane] = h * J.inv2;
-        }
-        rr->gx0[lane] = J.ox + c0;
-        rr->gy[lane] = J.oy + r;
-        rr->fa[lane] = fa - c0;
-        rr->fb[lane] = fb - c0;
+      for (int e = 0; e < 3; e++) {
+        float a, b, h;
+        edge_piece(J.t[2 * e] - fc0, J.t[2 * e + 1] - fr, J.t[(2 * e + 2) % 6] - fc0,
+                   J.t[(2 * e + 3) % 6] - fr, J.k[e], a, b, h);
+        rr->a[e][slot] = a;
+        rr->b[e][slot] = b;
+        rr->h[e][slot] = h * J.inv2;
       }
+      rr->gx0[slot] = J.ox + c0;
+      rr->gy[slot] = J.oy + r;
+      rr->fa[slot] = fa - c0;
+      rr->fb[slot] = fb - c0;
+      rr->st[slot] = pexcl;
     }
     __syncwarp();
-    // the partially covered pixels of these 32 rows, one per lane at a time
-    const int pincl = warp_incl_scan(np, lane);
-    const int ptotal = __shfl_sync(0xffffffffu, pincl, 31);
-    const int pexcl = pincl - np;
     for (int pbase = 0; pbase < ptotal; pbase += 32)
-      pixel_task(M, rr, pincl, pexcl, pbase + lane, ptotal);
-    __syncwarp();
+      pixel_task(M, rr, deal_owner_slot(np, pexcl, pbase, lane), pbase + lane, ptotal);
   }
+  __syncwarp();
 }
 
 // Per-warp queue of larger triangles in shared memory (capacity 64 >=
