@@ -40,7 +40,7 @@
 //     row adds the constant 1/|area| to its run of fully covered pixels
 //     through a per-row difference array, and the partially covered pixels
 //     of those rows are then dealt out one per lane and measured from the
-//     row's edge pieces (edge_piece, piece_mean).  Work is proportional to
+//     row's edge pieces (row_pieces, piece_mean).  Work is proportional to
 //     the perimeter, not the area, and no lane loops on its own.
 #pragma once
 #include <climits>
@@ -372,7 +372,7 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
 // boundary, as above): area(T n [0, 1]^2) is the sum over T's edges of the
 // integral over y in [0, 1] of clamp(x(y), 0, 1) along the edge, signed by
 // the direction of y.  The clamped y-range of an edge and its x there depend
-// only on the pixel row, so they are found once per row (edge_piece) and
+// only on the pixel row, so they are found once per row (row_pieces) and
 // each pixel of the row only shifts them by its column (piece_integral).
 
 // x on edge P -> Q (inverse slope k) at height y, extrapolated from the
@@ -382,18 +382,6 @@ __device__ __forceinline__ float edge_x_at(float y, float px, float py, float qx
                                           float k) {
   const float d1 = y - py, d2 = y - qy;
   return fabsf(d1) <= fabsf(d2) ? fmaf(d1, k, px) : fmaf(d2, k, qx);
-}
-
-// Piece of edge P -> Q (row-local coordinates) inside the band 0 <= y <= 1:
-// its x-range [a, b] and signed height h (all zero when it misses the band).
-__device__ __forceinline__ void edge_piece(float px, float py, float qx, float qy, float k,
-                                           float &a, float &b, float &h) {
-  const float ys = fminf(fmaxf(py, 0.f), 1.f), ye = fminf(fmaxf(qy, 0.f), 1.f);
-  const float xs = edge_x_at(ys, px, py, qx, qy, k), xe = edge_x_at(ye, px, py, qx, qy, k);
-  const bool cross = ye != ys;
-  a = cross ? fminf(xs, xe) : 0.f;
-  b = cross ? fmaxf(xs, xe) : 0.f;
-  h = cross ? ye - ys : 0.f;
 }
 
 // Mean of clamp(x, 0, 1) over x in [a, b] (a piece shifted to its pixel),
@@ -406,34 +394,47 @@ __device__ __forceinline__ float piece_mean(float a, float b) {
   return len > 0.f ? in * rcp_approx_f(len) : w;
 }
 
-// Frame row r of J: the columns [c0, c1] its band meets (widened by a small
-// margin; extra columns get zero area) and the fully covered run [fa, fb]
-// (empty when fa > fb), whose columns have all four corners in T (T convex):
-// fa >= both left ends and fb + 1 <= both right ends of T's chords on the
-// lines y = r and y = r + 1.
-__device__ __forceinline__ void tri_row_extent(const TriJob &J, int r, int &c0, int &c1,
-                                               int &fa, int &fb) {
+// Frame row r of J: each edge's piece inside the band r <= y <= r + 1
+// (x-range [a, b] and signed height h, all zero when it misses the band),
+// the columns [c0, c1] the band meets (widened by a small margin; extra
+// columns get zero area) and the fully covered run [fa, fb] (empty when
+// fa > fb), whose columns have all four corners in T (T convex): fa >= both
+// left ends and fb + 1 <= both right ends of T's chords on the lines y = r
+// and y = r + 1, which are the pieces' ends on those lines.
+__device__ __forceinline__ void row_pieces(const TriJob &J, int r, float (&a)[3], float (&b)[3],
+                                           float (&h)[3], int &c0, int &c1, int &fa, int &fb) {
   const float y0 = (float)r, y1 = (float)(r + 1);
+  float lo = 3.0e38f, hi = -3.0e38f;
   float l0 = 3.0e38f, h0 = -3.0e38f, l1 = 3.0e38f, h1 = -3.0e38f;
-  float bx0 = 3.0e38f, bx1 = -3.0e38f;
 #pragma unroll
   for (int e = 0; e < 3; e++) {
     const float px = J.t[2 * e], py = J.t[2 * e + 1];
-    const float qy = J.t[(2 * e + 3) % 6];
-    const float lo = fminf(py, qy), hi = fmaxf(py, qy);
-    if (lo < hi) {
-      const float xa = fmaf(y0 - py, J.k[e], px);
-      const float xb = fmaf(y1 - py, J.k[e], px);
-      if (lo <= y0 && y0 <= hi) l0 = fminf(l0, xa), h0 = fmaxf(h0, xa);
-      if (lo <= y1 && y1 <= hi) l1 = fminf(l1, xb), h1 = fmaxf(h1, xb);
+    const float qx = J.t[(2 * e + 2) % 6], qy = J.t[(2 * e + 3) % 6];
+    const float ys = fminf(fmaxf(py, y0), y1), ye = fminf(fmaxf(qy, y0), y1);
+    const float xs = edge_x_at(ys, px, py, qx, qy, J.k[e]);
+    const float xe = edge_x_at(ye, px, py, qx, qy, J.k[e]);
+    const bool cross = ye != ys;
+    a[e] = cross ? fminf(xs, xe) : 0.f;
+    b[e] = cross ? fmaxf(xs, xe) : 0.f;
+    h[e] = cross ? ye - ys : 0.f;
+    if (cross) lo = fminf(lo, a[e]), hi = fmaxf(hi, b[e]);
+    const float ylo = fminf(py, qy), yhi = fmaxf(py, qy);
+    if (ylo < yhi) {
+      if (ylo <= y0 && y0 <= yhi) {
+        const float x = ys == y0 ? xs : xe;
+        l0 = fminf(l0, x);
+        h0 = fmaxf(h0, x);
+      }
+      if (ylo <= y1 && y1 <= yhi) {
+        const float x = ys == y1 ? xs : xe;
+        l1 = fminf(l1, x);
+        h1 = fmaxf(h1, x);
+      }
     }
-    if (py >= y0 && py <= y1) bx0 = fminf(bx0, px), bx1 = fmaxf(bx1, px);
   }
-  bx0 = fminf(bx0, fminf(l0, l1));
-  bx1 = fmaxf(bx1, fmaxf(h0, h1));
   const float eps = 1e-3f, lim = 1.0e9f;
-  c0 = (int)floorf(fminf(fmaxf(bx0 - eps, -lim), lim));
-  c1 = (int)floorf(fminf(fmaxf(bx1 + eps, -lim), lim));
+  c0 = (int)floorf(fminf(fmaxf(lo - eps, -lim), lim));
+  c1 = (int)floorf(fminf(fmaxf(hi + eps, -lim), lim));
   fa = 1;
   fb = 0;
   if (h0 >= l0 && h1 >= l1) {
@@ -537,12 +538,13 @@ static __device__ __noinline__ void warp_tri_jobs(unsigned long long *acc,
     const int task = base + lane;
     const int o = deal_owner_slot(nrows, excl, base, lane);
     int np = 0, r = 0, c0 = 0, fa = 1, fb = 0, k = 0;
+    float pa[3], pb[3], ph[3];
     if (task < total) {
       k = rr->tk[o];
       r = rr->trl[o] + task - rr->tex[o];
       const TriJob &J = q[k];
       int c1;
-      tri_row_extent(J, r, c0, c1, fa, fb);
+      row_pieces(J, r, pa, pb, ph, c0, c1, fa, fb);
       c0 = max(c0, -J.ox);
       c1 = min(c1, M.npix - 1 - J.ox);
       fa = max(fa, c0);
@@ -567,15 +569,13 @@ static __device__ __noinline__ void warp_tri_jobs(unsigned long long *acc,
     __syncwarp();  // the previous round's readers are done with the records
     if (np > 0) {
       const TriJob &J = q[k];
-      const float fc0 = (float)c0, fr = (float)r;
+      const float fc0 = (float)c0;
 #pragma unroll
       for (int e = 0; e < 3; e++) {
-        float a, b, h;
-        edge_piece(J.t[2 * e] - fc0, J.t[2 * e + 1] - fr, J.t[(2 * e + 2) % 6] - fc0,
-                   J.t[(2 * e + 3) % 6] - fr, J.k[e], a, b, h);
-        rr->a[e][slot] = a;
-        rr->b[e][slot] = b;
-        rr->h[e][slot] = h * J.inv2;
+        // x relative to column c0 (zero-height pieces stay zero)
+        rr->a[e][slot] = ph[e] != 0.f ? pa[e] - fc0 : 0.f;
+        rr->b[e][slot] = ph[e] != 0.f ? pb[e] - fc0 : 0.f;
+        rr->h[e][slot] = ph[e] * J.inv2;
       }
       rr->gx0[slot] = J.ox + c0;
       rr->gy[slot] = J.oy + r;
