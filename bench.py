@@ -41,8 +41,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FMA lanes x 2 flops 
 
 # dram bytes per launch of k_shoot_ipm from one ncu capture (see profiles/),
 # valid only for the kernel sources it was taken on (hash below)
-NCU_TRAFFIC = {"sources_sha1": "19c54372c9e385881dda60a8a69bd74212ccb9cb",
-               "bytes_per_launch": 75.86e6 + 4.80e9}
+NCU_TRAFFIC = {"sources_sha1": "608d2e9ea40c6d135db683aa58e9fa298af4fc5f",
+               "bytes_per_launch": 79.99e6 + 4.85e9}
 
 
 def kernel_sources_sha1():
