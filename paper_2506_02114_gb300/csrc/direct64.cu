@@ -161,13 +161,14 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
                                                  tri ? cur : cur_r, ra, cnt, se, job)
                                   : TRI_DONE;
         wq_push(M, wq, code == TRI_SMALL, se, lane);
-        jq_push(M, jq, code == TRI_BIG, job, lane);
+        jq_add(jq, code == TRI_BIG, job, lane);
+        jq_share(M, jq, false, lane);
       }
       prev = cur;
     }
     run_flush(M, ra);
     wq_drain(M, wq, lane);
-    jq_drain(M, jq, lane);
+    jq_share(M, jq, true, lane);
   }
   unsigned v[MM_N_COUNTERS] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big, cnt.line};
 #pragma unroll

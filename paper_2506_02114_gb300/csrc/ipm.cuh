@@ -301,14 +301,10 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     if (gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix) run_add(M, ra, gy * M.npix + gx, MM_FIX_ONE);
     return TRI_DONE;
   }
-  // restrict to the map: frame columns [-ox, npix-1-ox]
-  const long long mcl = -(long long)ox, mch = (long long)M.npix - 1 - ox;
-  const long long mrl = -(long long)oy, mrh = (long long)M.npix - 1 - oy;
-  const long long cl = cx0 > mcl ? cx0 : mcl, ch = cx1 < mch ? cx1 : mch;
-  const long long rl = cy0 > mrl ? cy0 : mrl, rh = cy1 < mrh ? cy1 : mrh;
-  if (cl > ch || rl > rh) return TRI_DONE;  // misses the map
-  cnt.clipped++;
   if ((cx1 - cx0) + (cy1 - cy0) == 1) {
+    // (two adjacent pixels that passed the test above: at least one is in
+    // the map, so the map restriction below is not needed)
+    cnt.clipped++;
     // Two pixels split by one grid line u = L (u = x or y).  The vertex alone
     // on its side cuts off a triangle similar to the corner it spans, of
     // area fraction d^2 / ((u_a - u_l)(u_b - u_l)) with d = L - u_l (the two
@@ -316,8 +312,10 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     // in fixed point, so the pair sums to exactly one triangle.
     const int o = cy1 - cy0;  // 0: vertical line, 1: horizontal line
     const float L = (float)(o ? cy0 : cx0) + 1.f;
-    const unsigned long long vlow = low_side_fixed(t[o], t[2 + o], t[4 + o], L);
-    const bool b0 = t[o] < L;  // vertex a on the low side
+    // (selects, not t[o]: a run-time index would put t in local memory)
+    const float u0 = o ? t[1] : t[0], u1 = o ? t[3] : t[2], u2 = o ? t[5] : t[4];
+    const unsigned long long vlow = low_side_fixed(u0, u1, u2, L);
+    const bool b0 = u0 < L;  // vertex a on the low side
     // the pixel holding vertex a goes through the run accumulator
     const long long glx = (long long)ox + cx0, gly = (long long)oy + cy0;  // low pixel
     const long long gax = b0 ? glx : glx + 1 - o, gay = b0 ? gly : gly + o;
@@ -329,6 +327,13 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     cnt.line++;
     return TRI_DONE;
   }
+  // restrict to the map: frame columns [-ox, npix-1-ox]
+  const long long mcl = -(long long)ox, mch = (long long)M.npix - 1 - ox;
+  const long long mrl = -(long long)oy, mrh = (long long)M.npix - 1 - oy;
+  const long long cl = cx0 > mcl ? cx0 : mcl, ch = cx1 < mch ? cx1 : mch;
+  const long long rl = cy0 > mrl ? cy0 : mrl, rh = cy1 < mrh ? cy1 : mrh;
+  if (cl > ch || rl > rh) return TRI_DONE;  // misses the map
+  cnt.clipped++;
   if (cx1 - cx0 <= 1 && cy1 - cy0 <= 1) {
     se.ox = ox;
     se.oy = oy;
@@ -508,7 +513,7 @@ __device__ __forceinline__ void pixel_task(const MapAcc &M, const RowRecs *rr, i
 // partially covered pixels of those 32 rows are then dealt out one per lane.
 // Work is proportional to the perimeter, and the lanes stay busy however
 // the rows differ.  Call with all 32 lanes.
-static __device__ __noinline__ void warp_tri_jobs(unsigned long long *acc,
+__device__ __forceinline__ void warp_tri_jobs(unsigned long long *acc,
                                                   unsigned long long *span, int npix,
                                                   const TriJob *q, int nb, RowRecs *rr,
                                                   int lane) {
@@ -607,24 +612,25 @@ struct WarpSmem {
 };
 #define MM_SHOOT_SMEM_BYTES (8 * sizeof(WarpSmem))  // 8 warps per block
 
-__device__ __forceinline__ void jq_push(const MapDev &M, JobQueue &jq, bool want,
-                                        const TriJob &job, int lane) {
+// Queue the lanes' larger triangles (no processing).
+__device__ __forceinline__ void jq_add(JobQueue &jq, bool want, const TriJob &job, int lane) {
   const unsigned m = __ballot_sync(0xffffffffu, want);
   if (!m) return;
   const int pos = jq.n + __popc(m & ((1u << lane) - 1u));
   if (want) jq.q[pos] = job;
   jq.n += __popc(m);
   __syncwarp();
-  while (jq.n >= 32) {
-    jq.n -= 32;
-    warp_tri_jobs(M.acc, M.span, M.npix, jq.q + jq.n, 32, jq.rr, lane);
-  }
 }
 
-__device__ __forceinline__ void jq_drain(const MapDev &M, JobQueue &jq, int lane) {
-  if (jq.n > 0) warp_tri_jobs(M.acc, M.span, M.npix, jq.q, jq.n, jq.rr, lane);
-  jq.n = 0;
-  __syncwarp();
+// Share out full batches of 32 queued triangles, and with `flush` also the
+// rest.  The hot kernel calls this from one place only, so the dealing is
+// inlined once and no registers are saved around a call.
+__device__ __forceinline__ void jq_share(const MapDev &M, JobQueue &jq, bool flush, int lane) {
+  while (jq.n >= 32 || (flush && jq.n > 0)) {
+    const int nb = min(jq.n, 32);
+    jq.n -= nb;
+    warp_tri_jobs(M.acc, M.span, M.npix, jq.q + jq.n, nb, jq.rr, lane);
+  }
 }
 
 }  // namespace mm

@@ -241,13 +241,19 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
       if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
       prev = shoot_point<SQUARE, false>(M, leaf, i, jb, 0.f, 0.f, vvalid);
     }
-    for (int64_t j = jb + 1; j <= je; j++) {
-      const int cy = __ldg(&M.row_cell[j]);
-      const int leaf = lookup_leaf(M, cx, cy);
-      if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
-      Vtx cur = shoot_point<SQUARE, false>(M, leaf, i, j, 0.f, 0.f, vvalid);
-      Vtx cur_r = shfl_down_vtx(cur, 1);
-      Vtx prev_r = shfl_down_vtx(prev, 1);
+    // one pass more than there are cell rows: the last one maps nothing and
+    // shares out what is left in the queue of larger triangles
+    for (int64_t j = jb + 1;; j++) {
+      const bool fin = j > je;  // warp-uniform
+      Vtx cur = prev, cur_r = prev, prev_r = prev;
+      if (!fin) {
+        const int cy = __ldg(&M.row_cell[j]);
+        const int leaf = lookup_leaf(M, cx, cy);
+        if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
+        cur = shoot_point<SQUARE, false>(M, leaf, i, j, 0.f, 0.f, vvalid);
+        cur_r = shfl_down_vtx(cur, 1);
+        prev_r = shfl_down_vtx(prev, 1);
+      }
 #pragma unroll 1
       for (int tri = 0; tri < 2; tri++) {
         TriJob job;
@@ -262,15 +268,17 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
         vc.py = tri ? cur.py : cur_r.py;
         vc.fx = tri ? cur.fx : cur_r.fx;
         vc.fy = tri ? cur.fy : cur_r.fy;
-        const int code = cell_col ? ipm_triangle(M, prev, vb, vc, ra, cnt, se, job) : TRI_DONE;
+        const int code =
+            (cell_col && !fin) ? ipm_triangle(M, prev, vb, vc, ra, cnt, se, job) : TRI_DONE;
         wq_push(M, wq, code == TRI_SMALL, se, lane);
-        jq_push(M, jq, code == TRI_BIG, job, lane);
+        jq_add(jq, code == TRI_BIG, job, lane);
+        jq_share(M, jq, fin && tri == 1, lane);
       }
+      if (fin) break;
       prev = cur;
     }
     run_flush(M, ra);
     wq_drain(M, wq, lane);
-    jq_drain(M, jq, lane);
   }
   if (last_map >= 0) flush_counters(BATCH ? maps[last_map] : M1, cnt, lane);
 }
