@@ -159,6 +159,16 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
   return out;
 }
 
+// Whether both triangles of the cell (a, b, c, d) lie wholly beyond one
+// edge of the map, from the vertices' pixels alone (false when a vertex is
+// non-finite).
+__device__ __forceinline__ bool cell_beyond_map(const MapDev &M, const Vtx &a, const Vtx &b,
+                                                const Vtx &c, const Vtx &d) {
+  const int x0 = min(min(a.px, b.px), min(c.px, d.px)), x1 = max(max(a.px, b.px), max(c.px, d.px));
+  const int y0 = min(min(a.py, b.py), min(c.py, d.py)), y1 = max(max(a.py, b.py), max(c.py, d.py));
+  return x0 != MM_VTX_INVALID && (x1 < 0 || x0 >= M.npix || y1 < 0 || y0 >= M.npix);
+}
+
 __device__ __forceinline__ Vtx shfl_down_vtx(const Vtx &v, int d) {
   Vtx r;
   r.px = __shfl_down_sync(0xffffffffu, v.px, d);
@@ -253,6 +263,12 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
         cur = shoot_point<SQUARE, false>(M, leaf, i, j, 0.f, 0.f, vvalid);
         cur_r = shfl_down_vtx(cur, 1);
         prev_r = shfl_down_vtx(prev, 1);
+        // a row of cells all beyond the map (and none with a non-finite
+        // vertex, which must be counted) has nothing to map
+        if (__all_sync(0xffffffffu, !cell_col || cell_beyond_map(M, prev, prev_r, cur, cur_r))) {
+          prev = cur;
+          continue;
+        }
       }
 #pragma unroll 1
       for (int tri = 0; tri < 2; tri++) {
