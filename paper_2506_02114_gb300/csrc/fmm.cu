@@ -295,6 +295,9 @@ __global__ void k_near_count(TreeDev T, FmmConst C, int64_t n_rec, const int32_t
 // e_n = n d_n / (L_q delta), n = 2..p_eval, take coef_stride(p_eval) slots
 // (an even count, zero-padded) so the kernel loads them in pairs; its
 // direct stars are stored in its own grid frame.
+// NB >= p_eval bounds the coefficients at compile time, so they stay in
+// registers.
+template <int NB>
 __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
                                 const int32_t *active_list, const int32_t *near_off,
                                 const int32_t *near_cnt, const double2 *__restrict__ loc,
@@ -305,7 +308,7 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
   int64_t node;
   double zx, zy, L, cx, cy, Lq;
   sub_cell_geom(T, C, active_list, g, node, zx, zy, L, cx, cy, Lq);
-  const int p = C.p, P1 = p + 1, pe = min(C.p_eval, MM_PMAX), cs = coef_stride(pe);
+  const int p = C.p, P1 = p + 1, pe = min(C.p_eval, NB), cs = coef_stride(pe);
 
   // the grid vertex nearest the sub-cell centre
   const double gi = rint((cx - C.x0) / C.hx), gj = rint((cy - C.y0) / C.hy);
@@ -318,13 +321,17 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
   R.pad0 = R.pad1 = 0;
 
   // re-centred leaf expansion, d_1 .. d_pe
-  double2 d[MM_PMAX + 1];
+  double2 d[NB + 1];
   const double2 *c = loc + node * P1;
   const double ux = (cx - zx) / L, uy = (cy - zy) / L, r = Lq / L;
   double rn = 1.0;
-  for (int n = 1; n <= pe; n++) {
+#pragma unroll
+  for (int n = 1; n <= NB; n++) {
+    d[n] = make_double2(0.0, 0.0);
+    if (n > pe) continue;
     rn *= r;
     double sx = 0.0, sy = 0.0, px = 1.0, py = 0.0, binom = 1.0;  // u^(l-n), C(l, n)
+#pragma unroll 1
     for (int l = n; l <= p; l++) {
       const double2 cl = c[l];
       sx += binom * (cl.x * px - cl.y * py);
@@ -363,9 +370,12 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
             const double ix = Lq * dxs / den, iy = -Lq * dys / den;
             const double m = T.sm[i];
             double tx = ix, ty = iy;  // w^-n
-            for (int n = 1; n <= pe; n++) {
-              d[n].x -= m * tx / n;
-              d[n].y -= m * ty / n;
+#pragma unroll
+            for (int n = 1; n <= NB; n++) {
+              if (n <= pe) {
+                d[n].x -= m * tx / n;
+                d[n].y -= m * ty / n;
+              }
               const double ntx = tx * ix - ty * iy;
               ty = tx * iy + ty * ix;
               tx = ntx;
@@ -378,8 +388,10 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
   R.near_cnt = (int32_t)(k - R.near_off);
 
   const double s = 1.0 / (Lq * C.delta);
-  for (int n = 2; n <= pe; n++)
-    coef[g * cs + (n - 2)] = make_float2((float)(n * d[n].x * s), (float)(n * d[n].y * s));
+#pragma unroll
+  for (int n = 2; n <= NB; n++)
+    if (n <= pe)
+      coef[g * cs + (n - 2)] = make_float2((float)(n * d[n].x * s), (float)(n * d[n].y * s));
   for (int kk = pe - 1; kk < cs; kk++) coef[g * cs + kk] = make_float2(0.f, 0.f);
 
   // FP64 image of the sub-cell centre: macro model + sheet - far field there
@@ -526,9 +538,16 @@ cudaError_t launch_leaf_finalize(const TreeDev &T, const FmmConst &C, int64_t n_
                                  cudaStream_t st) {
   if (n_active <= 0) return cudaSuccess;
   const int64_t n = n_active << (2 * C.sub);
-  k_leaf_finalize<<<blocks_for(n, 64), 64, 0, st>>>(T, C, n, active_list, near_off,
-                                                    near_cnt, loc, leaf, near_pos, near_m, coef,
-                                                    err);
+  const unsigned nb = blocks_for(n, 64);
+  if (C.p_eval <= 16)
+    k_leaf_finalize<16><<<nb, 64, 0, st>>>(T, C, n, active_list, near_off, near_cnt, loc, leaf,
+                                           near_pos, near_m, coef, err);
+  else if (C.p_eval <= 32)
+    k_leaf_finalize<32><<<nb, 64, 0, st>>>(T, C, n, active_list, near_off, near_cnt, loc, leaf,
+                                           near_pos, near_m, coef, err);
+  else
+    k_leaf_finalize<MM_PMAX><<<nb, 64, 0, st>>>(T, C, n, active_list, near_off, near_cnt, loc,
+                                                leaf, near_pos, near_m, coef, err);
   return cudaGetLastError();
 }
 
