@@ -187,6 +187,9 @@ mm_status mm_create(double kappa_tot, double shear, double smooth_fraction,
  * deflection + inverse polygon mapping into a fixed-point accumulator, and
  * normalisation to magnification.  Asynchronous: returns once enqueued.
  * The caller synchronises the stream before reading results from the host.
+ * mm_create's plan already builds the tree and expansions for the handle's
+ * stars; the first run after it uses them (its tree and expansion stage
+ * times read 0) and every later run rebuilds them.
  */
 mm_status mm_run(mm_map *h, void *stream);
 

@@ -175,6 +175,7 @@ struct mm_map {
 
   int64_t launches = 0;   // library kernels launched by the last run
   bool prepared = false;  // tree + expansions current for the stars
+  bool fresh = false;     // mm_create's plan built them and no run has used them yet
   bool ran = false;
   bool timed_out = false;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -676,7 +677,14 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     LCH(launch_ipm_vertices(h->d_md.p, h->verts.p, h->col_hi - h->col_lo + 1, h->row_lo,
                             h->row_hi, h->counter.p, h->err.p, shoot_grid(), st));
   } else {
-    CKS(prepare(h, st));
+    // The plan of mm_create ran the whole tree and expansion pipeline on the
+    // same stars; the first run uses that result instead of repeating it.
+    if (h->fresh) {
+      h->fresh = false;
+      CKS(record(h, 1, st));
+    } else {
+      CKS(prepare(h, st));
+    }
     CKS(record(h, 2, st));
     const int64_t work = (int64_t)h->md.strips * h->md.row_blocks;
     LCH(launch_shoot_ipm(h->d_md.p, &h->md, 1, work, h->md.square_cells != 0, h->counter.p, h->err.p,
@@ -817,6 +825,7 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
     CKS(run_fmm(h, st, true));
     CK(cudaStreamSynchronize(st));
     h->prepared = true;
+    h->fresh = true;
   }
   fill_mapdev(h);
   CK(cudaMemcpyAsync(h->d_md.p, &h->md, sizeof(MapDev), cudaMemcpyHostToDevice, st));
@@ -876,7 +885,12 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
     h->launches = 0;
     CKS(record(h, 0, st));
     CKS(clear_map(h, st));
-    CKS(prepare(h, st));
+    if (h->fresh) {
+      h->fresh = false;
+      CKS(record(h, 1, st));
+    } else {
+      CKS(prepare(h, st));
+    }
     CKS(record(h, 2, st));
     mds[i] = h->md;
     mds[i].work_begin = work;
