@@ -245,28 +245,29 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
     const int cx = __ldg(&M.col_cell[vvalid ? i : M.col_end]);
     const bool cell_col = (lane < MM_STRIP) && (i < M.col_end);
     RunAcc ra = {-1, 0ull};
-    Vtx prev;
+    Vtx prev, prev_r;  // this lane's vertex of the previous row and its right neighbour's
     {
       const int leaf = lookup_leaf(M, cx, __ldg(&M.row_cell[jb]));
       if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
       prev = shoot_point<SQUARE, false>(M, leaf, i, jb, 0.f, 0.f, vvalid);
+      prev_r = shfl_down_vtx(prev, 1);
     }
     // one pass more than there are cell rows: the last one maps nothing and
     // shares out what is left in the queue of larger triangles
     for (int64_t j = jb + 1;; j++) {
       const bool fin = j > je;  // warp-uniform
-      Vtx cur = prev, cur_r = prev, prev_r = prev;
+      Vtx cur = prev, cur_r = prev_r;
       if (!fin) {
         const int cy = __ldg(&M.row_cell[j]);
         const int leaf = lookup_leaf(M, cx, cy);
         if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
         cur = shoot_point<SQUARE, false>(M, leaf, i, j, 0.f, 0.f, vvalid);
         cur_r = shfl_down_vtx(cur, 1);
-        prev_r = shfl_down_vtx(prev, 1);
         // a row of cells all beyond the map (and none with a non-finite
         // vertex, which must be counted) has nothing to map
         if (__all_sync(0xffffffffu, !cell_col || cell_beyond_map(M, prev, prev_r, cur, cur_r))) {
           prev = cur;
+          prev_r = cur_r;
           continue;
         }
       }
@@ -292,6 +293,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
       }
       if (fin) break;
       prev = cur;
+      prev_r = cur_r;
     }
     run_flush(M, ra);
     wq_drain(M, wq, lane);
