@@ -84,6 +84,14 @@ typedef struct {
                                21 tree levels. */
   int64_t col_begin;        /* shoot only cell columns [col_begin, col_end) of */
   int64_t col_end;          /*   the ray grid; both 0 -> every column */
+  int32_t no_cull;          /* FMM mode: 1 computes every vertex; 0 (default)
+                               skips vertex rows of the warp proven, from
+                               per-sub-cell bounds on the macro term, the
+                               evaluated series and the direct stars'
+                               deflection, to land beyond the same map edge
+                               as the row below (the map is unchanged: such
+                               cells lie wholly outside it) */
+  int32_t reserved;
 } mm_options;
 
 /* Every derived scalar of a run (host-side numbers; no GPU needed). */
@@ -132,6 +140,7 @@ typedef struct {
   int64_t triangles_quad;   /*   of which 2 x 2 pixels (both grid lines crossed) */
   int64_t triangles_box;    /*   of which with a box of at most 64 map pixels */
   int64_t triangles_rows;   /*   of which larger (pixel rows shared by a warp) */
+  int64_t rows_culled;      /* warp rows of vertices not computed (culling) */
   int64_t kernel_launches;  /* library kernels launched by the last run (CUB's
                                sort/scan kernels and memsets not counted) */
   /* stage times of the last mm_run in ms (time_stages = 1), else -1 */

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
                 ("flux_fraction_f", ctypes.c_double), ("center_y", ctypes.c_double * 2),
                 ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
                 ("rows_per_item", ctypes.c_int32), ("sub_levels", ctypes.c_int32),
-                ("col_begin", ctypes.c_int64), ("col_end", ctypes.c_int64)]
+                ("col_begin", ctypes.c_int64), ("col_end", ctypes.c_int64),
+                ("no_cull", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -73,6 +74,7 @@ class Stats(ctypes.Structure):
                 ("triangles_clipped", ctypes.c_int64), ("triangles_line", ctypes.c_int64),
                 ("triangles_quad", ctypes.c_int64),
                 ("triangles_box", ctypes.c_int64), ("triangles_rows", ctypes.c_int64),
+                ("rows_culled", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ms_tree", ctypes.c_double),
                 ("ms_expansions", ctypes.c_double), ("ms_shoot", ctypes.c_double),
                 ("ms_normalize", ctypes.c_double), ("ms_total", ctypes.c_double)]
@@ -162,7 +164,7 @@ def _ptr(a):
 
 def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=None,
                  flux_fraction_f=0.0, center_y=(0.0, 0.0), row_begin=0, row_end=0,
-                 rows_per_item=0, col_begin=0, col_end=0, sub_levels=0):
+                 rows_per_item=0, col_begin=0, col_end=0, sub_levels=0, cull=True):
     o = Options()
     o.mode = int(mode)
     o.time_stages = 1 if time_stages else 0
@@ -175,6 +177,7 @@ def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=No
     o.row_begin, o.row_end = int(row_begin), int(row_end)
     o.rows_per_item = int(rows_per_item)
     o.sub_levels = int(sub_levels)
+    o.no_cull = 0 if cull else 1
     o.col_begin, o.col_end = int(col_begin), int(col_end)
     return o
 

@@ -486,6 +486,8 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
   C.p = p;
   C.p_eval = h->p_eval;
   C.sub = h->sub;
+  C.npix = P.npix;
+  C.cull = h->opt.no_cull ? 0 : 1;
   C.kappa = P.kappa;
   C.gamma = P.gamma;
   C.kappa_star = P.kappa_star;
@@ -596,6 +598,7 @@ static void fill_mapdev(mm_map *h) {
   M.near_m = h->near_m.p;
   M.coef = h->coef.p;
   M.p = h->p_eval;
+  M.cull = h->opt.no_cull ? 0 : 1;
   M.sub = h->sub;
   M.node_level = h->lvl.p;
   M.square_cells = (P.h[0] == P.h[1]) ? 1 : 0;
@@ -1056,6 +1059,7 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
     out->triangles_box = (int64_t)st[3];
     out->triangles_rows = (int64_t)st[4];
     out->triangles_line = (int64_t)st[5];
+    out->rows_culled = (int64_t)st[6];
   }
   out->kernel_launches = h->launches;
   if (h->ev_recorded) {

@@ -318,7 +318,8 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
   R.j_ref = (int32_t)gj;
   R.fcx = (float)((cx - xr) / C.hx);
   R.fcy = (float)((cy - yr) / C.hy);
-  R.pad0 = R.pad1 = 0;
+  R.cull_side = MM_CULL_NONE;
+  R.cull_r2 = -1.f;
 
   // re-centred leaf expansion, d_1 .. d_pe
   double2 d[NB + 1];
@@ -348,6 +349,7 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
   // the direct ones never exceed the slots k_near_count reserved
   int64_t k = near_off[g];
   const int64_t kend = k + near_cnt[g];
+  double m_direct = 0.0;
   for_each_near_range(
       T, node,
       [&](int64_t b, int64_t e) {
@@ -363,6 +365,7 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
             np.fy = (float)(syg - Ky);
             near_pos[k] = np;
             near_m[k] = (float)T.sm[i];
+            m_direct += T.sm[i];
             k++;
           } else {
             // 1/w = L_q / (z_i - z_q)
@@ -412,6 +415,42 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
   R.zsy = (float)(C.hy / Lq);
   R.coef_off = (int32_t)(g * cs);
   R.node = (int32_t)node;
+
+  // Culling bounds.  A vertex of this sub-cell (grid offset within
+  // L_s + h of its centre) lands at the centre's image plus the macro term,
+  // the evaluated far-field series and the direct stars' deflection, all in
+  // pixels.  The first two stay within a box of half-widths B about (U, V):
+  // |macro| <= |1 - kappa + kappa_* +- gamma| (L_s + h)/delta and
+  // |series| <= sum_n |e_n| zeta_max^(n-1) over the stored coefficients.  If
+  // that box lies D pixels beyond a map edge, a vertex whose direct stars
+  // are all farther than M_direct / (delta (D - margin)) is deflected by
+  // them less than D - margin, so it lands beyond that edge too.
+  if (C.cull) {
+    const double ak = 1.0 - C.kappa + C.kappa_star;
+    const double hmax = fmax(C.hx, C.hy);
+    const double zmax = sqrt(2.0) * (Lq + hmax) / Lq;
+    double F = 0.0, zp = 1.0;
+#pragma unroll
+    for (int n = 2; n <= NB; n++) {
+      zp *= zmax;  // zeta_max^(n-1)
+      if (n <= pe) F += hypot(n * d[n].x * s, n * d[n].y * s) * zp;
+    }
+    F *= 1.01;
+    const double Bu = fabs(ak + C.gamma) * (Lq + hmax) / C.delta + F;
+    const double Bv = fabs(ak - C.gamma) * (Lq + hmax) / C.delta + F;
+    const double Uc = U, Vc = V, n = (double)C.npix, margin = 2.0;
+    const double Dl = -(Uc + Bu), Dr = (Uc - Bu) - n, Db = -(Vc + Bv), Dt = (Vc - Bv) - n;
+    double D = Dl;
+    int side = MM_CULL_LEFT;
+    if (Dr > D) D = Dr, side = MM_CULL_RIGHT;
+    if (Db > D) D = Db, side = MM_CULL_BOTTOM;
+    if (Dt > D) D = Dt, side = MM_CULL_TOP;
+    if (D > 2.0 * margin && U > -1.9e8 && U < 1.9e8 && V > -1.9e8 && V < 1.9e8) {
+      const double rc = m_direct / (C.delta * (D - margin) * C.hx);  // grid units of h_x
+      R.cull_side = side;
+      R.cull_r2 = (float)(rc * rc * 1.01);
+    }
+  }
   leaf[g] = R;
 }
 

@@ -235,10 +235,11 @@ __device__ __forceinline__ void wq_drain(const MapDev &M, WarpQueue &wq, int lan
 // Per-lane triangle counters, reduced per warp into MapDev::stat:
 // [0] dropped, [1] multi-pixel (clipped) in the map, [2] within a 2 x 2 box
 // crossing both grid lines, [3] box of at most MM_MED_PIXELS pixels (pixel
-// jobs), [4] larger (row jobs), [5] two pixels split by one grid line.
-#define MM_N_COUNTERS 6
+// jobs), [4] larger (row jobs), [5] two pixels split by one grid line, [6]
+// vertex rows not computed because culling proved them beyond the map.
+#define MM_N_COUNTERS 7
 struct IpmCounters {
-  unsigned dropped, clipped, small, strip, big, line;
+  unsigned dropped, clipped, small, strip, big, line, culled;
 };
 
 // A triangle shared out to the whole warp: frame pixel, frame coordinates,

@@ -43,8 +43,15 @@ struct __align__(16) LeafRec {
   int32_t near_off, near_cnt; // the sub-cell's direct-sum stars in near_pos/near_m
   int32_t coef_off;           // first of coef_stride(p_eval) far-field coefficient slots
   int32_t node;               // tree node id of the leaf
-  int32_t pad0, pad1;
+  // Culling: every vertex of the sub-cell whose squared distance |g|^2 (grid
+  // units, as the near field measures it) to each direct star exceeds
+  // cull_r2 lands beyond map edge cull_side (MM_CULL_*); 0: no guarantee.
+  int32_t cull_side;
+  float cull_r2;
 };
+
+// Map edges a culled vertex lies beyond.
+enum { MM_CULL_NONE = 0, MM_CULL_LEFT = 1, MM_CULL_RIGHT = 2, MM_CULL_BOTTOM = 3, MM_CULL_TOP = 4 };
 
 // Direct-sum star in its record's grid frame: grid position relative to
 // (i_ref, j_ref) = (Kx + fx, Ky + fy), K integer-valued, |f| <= 0.5.
@@ -82,6 +89,7 @@ struct MapDev {
   const float *near_m;
   const float2 *coef;
   int32_t p;                  // terms of the re-centred expansion evaluated per ray
+  int32_t cull;               // 1: skip the deflection of vertex rows proven beyond the map
   int32_t square_cells;       // 1 when h_x == h_y
   // per-ray constants (pixel units)
   float A1, A2;               // (1 - kappa + kappa_star +- gamma) h / delta

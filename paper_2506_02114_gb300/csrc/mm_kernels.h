@@ -60,6 +60,8 @@ struct FmmConst {
   int p;                      // expansion order of the FMM
   int p_eval;                 // terms kept of each sub-cell's re-centred expansion
   int sub;                    // sub-cell levels s: 4^s sub-cells per leaf
+  int npix;                   // map pixels per side (culling bounds)
+  int cull;                   // 1: compute the culling bounds
   double kappa, gamma, kappa_star;
   double x0, y0, hx, hy;      // ray grid
   double lox, loy, delta;     // map lower-left corner and pixel side

@@ -159,6 +159,39 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
   return out;
 }
 
+// Map edge that vertex (i, j) of record `leaf` is proven to land beyond
+// (MM_CULL_*), from the record's culling bound and the vertex's distances to
+// the record's direct stars, measured as the near field measures them;
+// MM_CULL_NONE when not proven.
+template <bool SQUARE>
+__device__ __forceinline__ int vertex_cull_side(const MapDev &M, int leaf, int64_t i, int64_t j) {
+  if (leaf < 0) return MM_CULL_NONE;
+  const int4 *rp = reinterpret_cast<const int4 *>(M.leaf + leaf);
+  const int4 q3 = __ldg(rp + 3);
+  if (q3.z == MM_CULL_NONE) return MM_CULL_NONE;
+  const int4 q0 = __ldg(rp), q2 = __ldg(rp + 2);
+  const float r2 = __int_as_float(q3.w);
+  const float fi = (float)(int)(i - q0.x), fj = (float)(int)(j - q0.y);
+  const float4 *np_ = reinterpret_cast<const float4 *>(M.near_pos) + q2.z;
+  for (int k = 0; k < q2.w; k++) {
+    const float4 s = __ldg(np_ + k);
+    const float dx = (fi - s.x) - s.y, dy = (fj - s.z) - s.w;
+    const float r = SQUARE ? fmaf(dx, dx, dy * dy) : fmaf(dx, dx, M.rho * dy * dy);
+    if (!(r > r2)) return MM_CULL_NONE;
+  }
+  return q3.z;
+}
+
+// The map edge a whole row of the warp's vertices is proven to lie beyond
+// (lanes without a vertex agree with anything); MM_CULL_NONE otherwise.
+template <bool SQUARE>
+__device__ __forceinline__ int row_cull_side(const MapDev &M, int leaf, int64_t i, int64_t j,
+                                             bool vvalid) {
+  const int s = vvalid ? vertex_cull_side<SQUARE>(M, leaf, i, j) : -1;
+  const int S = __reduce_max_sync(0xffffffffu, s);
+  return (S > 0 && __all_sync(0xffffffffu, s == S || s < 0)) ? S : MM_CULL_NONE;
+}
+
 // Whether both triangles of the cell (a, b, c, d) lie wholly beyond one
 // edge of the map, from the vertices' pixels alone (false when a vertex is
 // non-finite).
@@ -180,13 +213,14 @@ __device__ __forceinline__ Vtx shfl_down_vtx(const Vtx &v, int d) {
 
 // Warp-reduce the per-lane triangle counters into the map's statistics.
 __device__ __forceinline__ void flush_counters(const MapDev &M, IpmCounters &cnt, int lane) {
-  unsigned v[MM_N_COUNTERS] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip, cnt.big, cnt.line};
+  unsigned v[MM_N_COUNTERS] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip,
+                               cnt.big,     cnt.line,    cnt.culled};
 #pragma unroll
   for (int k = 0; k < MM_N_COUNTERS; k++) {
     for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);
     if (lane == 0 && v[k]) atomicAdd(&M.stat[k], (unsigned long long)v[k]);
   }
-  cnt = IpmCounters{0u, 0u, 0u, 0u, 0u, 0u};
+  cnt = IpmCounters{0u, 0u, 0u, 0u, 0u, 0u, 0u};
 }
 
 // Persistent warps; each work item is a strip of 31 cell columns by
@@ -211,7 +245,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
   WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
   WarpQueue wq = {ws->quad, 0};
   JobQueue jq = {ws->big, &ws->rows, 0};
-  IpmCounters cnt = {0, 0, 0, 0, 0, 0};
+  IpmCounters cnt = {0, 0, 0, 0, 0, 0, 0};
   int last_map = -1;
   while (true) {
     unsigned long long w = 0;
@@ -246,21 +280,44 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
     const bool cell_col = (lane < MM_STRIP) && (i < M.col_end);
     RunAcc ra = {-1, 0ull};
     Vtx prev, prev_r;  // this lane's vertex of the previous row and its right neighbour's
+    // culling state of the previous row (warp-uniform): the map edge it is
+    // proven to lie beyond, and whether its vertices were computed
+    int prev_side = MM_CULL_NONE;
+    bool prev_exact = true;
     {
       const int leaf = lookup_leaf(M, cx, __ldg(&M.row_cell[jb]));
       if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
       prev = shoot_point<SQUARE, false>(M, leaf, i, jb, 0.f, 0.f, vvalid);
       prev_r = shfl_down_vtx(prev, 1);
+      if (M.cull) prev_side = row_cull_side<SQUARE>(M, leaf, i, jb, vvalid);
     }
     // one pass more than there are cell rows: the last one maps nothing and
     // shares out what is left in the queue of larger triangles
     for (int64_t j = jb + 1;; j++) {
       const bool fin = j > je;  // warp-uniform
       Vtx cur = prev, cur_r = prev_r;
+      int side = MM_CULL_NONE;
       if (!fin) {
         const int cy = __ldg(&M.row_cell[j]);
         const int leaf = lookup_leaf(M, cx, cy);
         if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
+        if (M.cull) {
+          side = row_cull_side<SQUARE>(M, leaf, i, j, vvalid);
+          if (side != MM_CULL_NONE && side == prev_side) {
+            // this row and the one below lie beyond the same map edge: the
+            // cells between them map nothing, and this row is not computed
+            prev_exact = false;
+            if (lane == 0) cnt.culled++;
+            continue;
+          }
+          if (!prev_exact) {
+            // the row below was not computed; its cells with this row are needed
+            const int lp = lookup_leaf(M, cx, __ldg(&M.row_cell[j - 1]));
+            prev = shoot_point<SQUARE, false>(M, lp, i, j - 1, 0.f, 0.f, vvalid);
+            prev_r = shfl_down_vtx(prev, 1);
+            prev_exact = true;
+          }
+        }
         cur = shoot_point<SQUARE, false>(M, leaf, i, j, 0.f, 0.f, vvalid);
         cur_r = shfl_down_vtx(cur, 1);
         // a row of cells all beyond the map (and none with a non-finite
@@ -268,6 +325,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
         if (__all_sync(0xffffffffu, !cell_col || cell_beyond_map(M, prev, prev_r, cur, cur_r))) {
           prev = cur;
           prev_r = cur_r;
+          prev_side = side;
           continue;
         }
       }
@@ -294,6 +352,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
       if (fin) break;
       prev = cur;
       prev_r = cur_r;
+      prev_side = side;
     }
     run_flush(M, ra);
     wq_drain(M, wq, lane);

@@ -210,3 +210,25 @@ def test_full_size_fmm_workload_sampled(oracle_mod):
     # footprint's edge), so the error is measured against max(mu_ref, |mu_macro|)
     e = band_errors(mub, mub_ref, p.mu_macro)
     assert e["p999"] <= MAP_P999_TOL and e["mean_rel"] <= MEAN_TOL, e
+
+
+def test_culling_leaves_the_map_unchanged():
+    """Culling skips the vertex rows proven (per-sub-cell bounds) to land
+    beyond the same map edge as the row below; the cells between such rows
+    lie wholly outside the map, so the fixed-point map of the full benchmark
+    workload is bit-identical to computing every vertex."""
+    wl = synthetic.workload("fmm_fp32_salpeter_2000")
+    m, pos = wl.stars()
+    args = (wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, wl.npix, wl.rays_per_pixel)
+    fixed, stats = [], []
+    for cull in (True, False):
+        h = mm.create(*args, fmm_order=wl.fmm_order, cull=cull)
+        mm.run(h, 0)
+        fixed.append(mm.get_map_fixed(h))
+        stats.append(mm.get_stats(h))
+        mm.destroy(h)
+    assert stats[0]["rows_culled"] > 0 and stats[1]["rows_culled"] == 0
+    for k in ("triangles_clipped", "triangles_line", "triangles_quad", "triangles_box",
+              "triangles_rows", "triangles_dropped"):
+        assert stats[0][k] == stats[1][k], k
+    assert np.array_equal(fixed[0], fixed[1])
