@@ -162,9 +162,15 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
 // Map edge that vertex (i, j) of record `leaf` is proven to land beyond
 // (MM_CULL_*), from the record's culling bound and the vertex's distances to
 // the record's direct stars, measured as the near field measures them;
-// MM_CULL_NONE when not proven.
+// MM_CULL_NONE when not proven.  `run` receives how many rows from j on
+// (this one included) the proof holds for: the column's vertices stay in
+// the sub-cell (below its upper edge, with a row to spare) and outside the
+// culling radius of every direct star (a star above is approached by one
+// row per row; one below or level only recedes).
 template <bool SQUARE>
-__device__ __forceinline__ int vertex_cull_side(const MapDev &M, int leaf, int64_t i, int64_t j) {
+__device__ __forceinline__ int vertex_cull_side(const MapDev &M, int leaf, int64_t i, int64_t j,
+                                                int &run) {
+  run = 0;
   if (leaf < 0) return MM_CULL_NONE;
   const int4 *rp = reinterpret_cast<const int4 *>(M.leaf + leaf);
   const int4 q3 = __ldg(rp + 3);
@@ -172,23 +178,35 @@ __device__ __forceinline__ int vertex_cull_side(const MapDev &M, int leaf, int64
   const int4 q0 = __ldg(rp), q2 = __ldg(rp + 2);
   const float r2 = __int_as_float(q3.w);
   const float fi = (float)(int)(i - q0.x), fj = (float)(int)(j - q0.y);
+  // rows to the sub-cell's upper edge (centre + half-length, grid units)
+  const float top = __int_as_float(q0.w) + 1.0f / __int_as_float(q2.y);
+  int n = (int)floorf(fminf(top - fj, 1.0e6f)) - 1;
+  const float rho = SQUARE ? 1.f : M.rho;
   const float4 *np_ = reinterpret_cast<const float4 *>(M.near_pos) + q2.z;
   for (int k = 0; k < q2.w; k++) {
     const float4 s = __ldg(np_ + k);
     const float dx = (fi - s.x) - s.y, dy = (fj - s.z) - s.w;
-    const float r = SQUARE ? fmaf(dx, dx, dy * dy) : fmaf(dx, dx, M.rho * dy * dy);
-    if (!(r > r2)) return MM_CULL_NONE;
+    const float dx2 = dx * dx;
+    if (!(fmaf(rho * dy, dy, dx2) > r2)) return MM_CULL_NONE;
+    if (dx2 > r2 || dy >= 0.f) continue;
+    // rows until |dy| falls to sqrt((r2 - dx^2) / rho), less one to spare
+    const float kin = -dy - sqrtf((r2 - dx2) / rho);
+    n = min(n, (int)floorf(kin) - 1);
   }
+  run = max(n, 1);
   return q3.z;
 }
 
 // The map edge a whole row of the warp's vertices is proven to lie beyond
-// (lanes without a vertex agree with anything); MM_CULL_NONE otherwise.
+// (lanes without a vertex agree with anything), and the rows from j on the
+// proof holds for in every lane; MM_CULL_NONE otherwise.
 template <bool SQUARE>
 __device__ __forceinline__ int row_cull_side(const MapDev &M, int leaf, int64_t i, int64_t j,
-                                             bool vvalid) {
-  const int s = vvalid ? vertex_cull_side<SQUARE>(M, leaf, i, j) : -1;
+                                             bool vvalid, int &run) {
+  int r = 1 << 30;
+  const int s = vvalid ? vertex_cull_side<SQUARE>(M, leaf, i, j, r) : -1;
   const int S = __reduce_max_sync(0xffffffffu, s);
+  run = (int)__reduce_min_sync(0xffffffffu, (unsigned)r);
   return (S > 0 && __all_sync(0xffffffffu, s == S || s < 0)) ? S : MM_CULL_NONE;
 }
 
@@ -289,7 +307,8 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
       if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
       prev = shoot_point<SQUARE, false>(M, leaf, i, jb, 0.f, 0.f, vvalid);
       prev_r = shfl_down_vtx(prev, 1);
-      if (M.cull) prev_side = row_cull_side<SQUARE>(M, leaf, i, jb, vvalid);
+      int run;
+      if (M.cull) prev_side = row_cull_side<SQUARE>(M, leaf, i, jb, vvalid, run);
     }
     // one pass more than there are cell rows: the last one maps nothing and
     // shares out what is left in the queue of larger triangles
@@ -302,12 +321,16 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
         const int leaf = lookup_leaf(M, cx, cy);
         if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
         if (M.cull) {
-          side = row_cull_side<SQUARE>(M, leaf, i, j, vvalid);
+          int run;
+          side = row_cull_side<SQUARE>(M, leaf, i, j, vvalid, run);
           if (side != MM_CULL_NONE && side == prev_side) {
-            // this row and the one below lie beyond the same map edge: the
-            // cells between them map nothing, and this row is not computed
+            // rows j .. j + run - 1 and the one below lie beyond the same map
+            // edge: the cells between them map nothing, and none of those
+            // rows is computed
+            const int64_t skip = min((int64_t)run, je - j + 1);
             prev_exact = false;
-            if (lane == 0) cnt.culled++;
+            if (lane == 0) cnt.culled += (unsigned)skip;
+            j += skip - 1;
             continue;
           }
           if (!prev_exact) {
