@@ -41,8 +41,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FMA lanes x 2 flops 
 
 # dram bytes per launch of k_shoot_ipm from one ncu capture (see profiles/),
 # valid only for the kernel sources it was taken on (hash below)
-NCU_TRAFFIC = {"sources_sha1": "608d2e9ea40c6d135db683aa58e9fa298af4fc5f",
-               "bytes_per_launch": 79.99e6 + 4.85e9}
+NCU_TRAFFIC = {"sources_sha1": "8ccbdf8ad75653c7b857c1a230e608c23c4bbb21",
+               "bytes_per_launch": 79.14e6 + 4.55e9}
 
 
 def kernel_sources_sha1():
@@ -299,13 +299,17 @@ def run_native(args):
     # near field + local expansion (p_e terms about the sub-cell centre) + macro + IPM test
     flops_per_ray = 11.0 * st["mean_near_stars"] + 8.0 * (pe - 1) + 8.0 + 20.0
     shoot_s = float(np.mean(shoot_ms)) * 1e-3
-    achieved = rays * flops_per_ray / shoot_s / 1e12
+    # vertices whose deflection culling proved unnecessary are not computed:
+    # a culled warp row skips the 31 vertex columns of its work item
+    computed = max(0, rays - 31 * st["rows_culled"])
+    achieved = computed * flops_per_ray / shoot_s / 1e12
     traffic = None
     if NCU_TRAFFIC["sources_sha1"] == kernel_sources_sha1():
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "k_shoot_ipm", "flops_per_ray": flops_per_ray,
+                "rays_computed": computed,
                 "kernel_ms": shoot_s * 1e3,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
