@@ -164,6 +164,9 @@ struct mm_map {
 
   // map
   DBuf<unsigned long long> acc, span, stat, counter, fixed_out;
+  DBuf<char> bigq;                     // larger triangles for the second IPM pass
+  DBuf<unsigned long long> bigq_n;     // [0] queued, [1] batches taken
+  int64_t bigq_cap = 0;
   DBuf<unsigned> err;
   DBuf<float> map;
   DBuf<MapDev> d_md;
@@ -612,6 +615,9 @@ static void fill_mapdev(mm_map *h) {
   M.acc = h->acc.p;
   M.span = h->span.p;
   M.stat = h->stat.p;
+  M.bigq = reinterpret_cast<TriJob *>(h->bigq.p);
+  M.bigq_n = h->bigq_n.p;
+  M.bigq_cap = h->bigq_cap;
 }
 
 static mm_status clear_map(mm_map *h, cudaStream_t st) {
@@ -621,6 +627,7 @@ static mm_status clear_map(mm_map *h, cudaStream_t st) {
                      st));
   CK(cudaMemsetAsync(h->stat.p, 0, 8 * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(h->counter.p, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(h->bigq_n.p, 0, 2 * sizeof(unsigned long long), st));
   return MM_OK;
 }
 
@@ -635,6 +642,14 @@ static mm_status alloc_map_buffers(mm_map *h) {
   CK(h->map.ensure(np));
   CK(h->stat.ensure(8));
   CK(h->counter.ensure(1));
+  // queue for the second IPM pass: 1 slot per 12 cells, 2^16 .. 2^27 slots
+  // (48 B each); batches that do not fit are dealt out by the first kernel
+  {
+    const int64_t cells = (h->col_hi - h->col_lo) * (h->row_hi - h->row_lo);
+    h->bigq_cap = std::min<int64_t>(int64_t(1) << 27, std::max<int64_t>(int64_t(1) << 16, cells / 12));
+    CK(h->bigq.ensure((size_t)h->bigq_cap * MM_TRIJOB_BYTES));
+    CK(h->bigq_n.ensure(2));
+  }
   CK(h->err.ensure(1));
   CK(cudaMemset(h->err.p, 0, sizeof(unsigned)));  // read after the plan in every mode
   CK(h->d_md.ensure(1));
@@ -693,6 +708,7 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     LCH(launch_shoot_ipm(h->d_md.p, &h->md, 1, work, h->md.square_cells != 0, h->counter.p, h->err.p,
                         shoot_grid(), st));
   }
+  LCH(launch_big_ipm(h->md, st));
   CKS(record(h, 3, st));
   LCH(launch_normalize(h->acc.p, h->span.p, P.npix, map_scale(P), h->map.p, st));
   CKS(record(h, 4, st));
@@ -908,6 +924,7 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
   lead->launches++;
   for (int i = 0; i < n; i++) {
     mm_map *h = hs[i];
+    LCH(launch_big_ipm(h->md, st));
     CKS(record(h, 3, st));
     LCH(launch_normalize(h->acc.p, h->span.p, h->P.npix, map_scale(h->P), h->map.p, st));
     CKS(record(h, 4, st));
@@ -1088,6 +1105,8 @@ void mm_destroy(mm_map *h) {
   for (auto *b : dbs) b->release();
   h->keys_in.release();
   h->keys.release();
+  h->bigq.release();
+  h->bigq_n.release();
   h->idx_in.release();
   h->idx.release();
   h->cub_tmp.release();

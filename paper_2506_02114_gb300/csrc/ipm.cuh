@@ -251,6 +251,7 @@ struct __align__(16) TriJob {
   float inv2;
   float k[3];
 };
+static_assert(sizeof(TriJob) == MM_TRIJOB_BYTES, "TriJob layout");
 
 enum { TRI_DONE = 0, TRI_SMALL = 1, TRI_BIG = 2 };
 
@@ -613,6 +614,17 @@ struct WarpSmem {
 };
 #define MM_SHOOT_SMEM_BYTES (8 * sizeof(WarpSmem))  // 8 warps per block
 
+// A queue entry with no pixel rows (frame far below any map).
+__device__ __forceinline__ TriJob empty_job_impl() {
+  TriJob e;
+  e.ox = e.oy = -(1 << 30);
+#pragma unroll
+  for (int k = 0; k < 6; k++) e.t[k] = 0.f;
+  e.inv2 = 0.f;
+  e.k[0] = e.k[1] = e.k[2] = 0.f;
+  return e;
+}
+
 // Queue the lanes' larger triangles (no processing).
 __device__ __forceinline__ void jq_add(JobQueue &jq, bool want, const TriJob &job, int lane) {
   const unsigned m = __ballot_sync(0xffffffffu, want);
@@ -623,15 +635,30 @@ __device__ __forceinline__ void jq_add(JobQueue &jq, bool want, const TriJob &jo
   __syncwarp();
 }
 
-// Share out full batches of 32 queued triangles, and with `flush` also the
-// rest.  The hot kernel calls this from one place only, so the dealing is
-// inlined once and no registers are saved around a call.
+// Full batches of 32 queued triangles (with `flush` also the rest) go to
+// the map's device queue for the larger-triangle kernel (k_big_ipm), which
+// deals them out at a higher occupancy than this kernel's; a batch that
+// does not fit is dealt out here, its reserved queue slots filled with
+// empty jobs.
 __device__ __forceinline__ void jq_share(const MapDev &M, JobQueue &jq, bool flush, int lane) {
   while (jq.n >= 32 || (flush && jq.n > 0)) {
     const int nb = min(jq.n, 32);
     jq.n -= nb;
-    warp_tri_jobs(M.acc, M.span, M.npix, jq.q + jq.n, nb, jq.rr, lane);
+    unsigned long long base = 0;
+    if (M.bigq_cap > 0) {
+      if (lane == 0) base = atomicAdd(M.bigq_n, (unsigned long long)nb);
+      base = __shfl_sync(0xffffffffu, base, 0);
+    }
+    if (M.bigq_cap > 0 && base + nb <= (unsigned long long)M.bigq_cap) {
+      if (lane < nb) M.bigq[base + lane] = jq.q[jq.n + lane];
+      __syncwarp();
+    } else {
+      if (M.bigq_cap > 0 && lane < nb && base + lane < (unsigned long long)M.bigq_cap)
+        M.bigq[base + lane] = empty_job_impl();
+      warp_tri_jobs(M.acc, M.span, M.npix, jq.q + jq.n, nb, jq.rr, lane);
+    }
   }
 }
+
 
 }  // namespace mm

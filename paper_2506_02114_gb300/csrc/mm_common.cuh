@@ -66,6 +66,9 @@ struct __align__(16) Vtx {
   float fx, fy;
 };
 
+struct TriJob;  // a triangle larger than 2 x 2 pixels (ipm.cuh)
+#define MM_TRIJOB_BYTES 48
+
 // Everything the deflection + mapping kernel needs about one map.
 struct MapDev {
   // ray grid
@@ -101,6 +104,10 @@ struct MapDev {
   unsigned long long *span;   // npix*(npix+1) row difference array
   // statistics (per map)
   unsigned long long *stat;   // triangle counters, see IpmCounters
+  // larger triangles handed to the second kernel (capacity 0: none)
+  TriJob *bigq;
+  unsigned long long *bigq_n; // [0] triangles queued, [1] the second kernel's batch counter
+  int64_t bigq_cap;
 };
 
 // Far-field coefficient slots per sub-cell record: the p_eval - 1

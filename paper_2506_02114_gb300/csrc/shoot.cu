@@ -383,6 +383,31 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
   if (last_map >= 0) flush_counters(BATCH ? maps[last_map] : M1, cnt, lane);
 }
 
+// Second pass over the larger triangles k_shoot_ipm (or k_ipm_vertices)
+// queued for the map: each warp takes batches of 32 from the device queue
+// and deals out their pixel rows and partially covered pixels
+// (warp_tri_jobs), at 4 blocks per SM where the first kernel runs 2.
+#define MM_BIG_MINB 4
+__global__ void __launch_bounds__(256, MM_BIG_MINB) k_big_ipm(const MapDev M) {
+  __shared__ TriJob q[8][32];
+  __shared__ RowRecs rr[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned long long cap = (unsigned long long)M.bigq_cap;
+  const unsigned long long qn = *M.bigq_n;
+  const long long n = (long long)(qn < cap ? qn : cap);
+  while (true) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(M.bigq_n + 1, 1ull);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    const long long base = (long long)b * 32;
+    if (base >= n) break;
+    const int nb = (int)min(32ll, n - base);
+    if (lane < nb) q[w][lane] = M.bigq[base + lane];
+    __syncwarp();
+    warp_tri_jobs(M.acc, M.span, M.npix, q[w], nb, &rr[w], lane);
+  }
+}
+
 // mu = (acc + row-prefix(span)) * 2^-32 * (h_x h_y / 2) / delta^2; one block
 // per map row.
 __global__ void __launch_bounds__(256) k_normalize(const unsigned long long *__restrict__ acc,
@@ -491,6 +516,15 @@ cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n
                                              st)
                 : launch_shoot_t<false, true>(d_maps, none, n_maps, total_work, counter, err,
                                               grid, st);
+}
+
+cudaError_t launch_big_ipm(const MapDev &m, cudaStream_t st) {
+  if (m.bigq_cap <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_big_ipm<<<sms * MM_BIG_MINB, 256, 0, st>>>(m);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_normalize(const unsigned long long *acc, const unsigned long long *span,
