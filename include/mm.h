@@ -143,8 +143,11 @@ typedef struct {
   int64_t rows_culled;      /* warp rows of vertices not computed (culling) */
   int64_t kernel_launches;  /* library kernels launched by the last run (CUB's
                                sort/scan kernels and memsets not counted) */
-  /* stage times of the last mm_run in ms (time_stages = 1), else -1 */
+  /* stage times of the last mm_run in ms (time_stages = 1), else -1;
+     ms_shoot = ms_first_pass (deflection and the one-, two- and 2x2-pixel
+     triangles) + ms_second_pass (the queued larger triangles) */
   double ms_tree, ms_expansions, ms_shoot, ms_normalize, ms_total;
+  double ms_first_pass, ms_second_pass;
 } mm_stats;
 
 /*

@@ -77,7 +77,8 @@ class Stats(ctypes.Structure):
                 ("rows_culled", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ms_tree", ctypes.c_double),
                 ("ms_expansions", ctypes.c_double), ("ms_shoot", ctypes.c_double),
-                ("ms_normalize", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("ms_normalize", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_first_pass", ctypes.c_double), ("ms_second_pass", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "params"}

@@ -181,7 +181,9 @@ struct mm_map {
   bool fresh = false;     // mm_create's plan built them and no run has used them yet
   bool ran = false;
   bool timed_out = false;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // stage events: start, tree, expansions, mapping done, normalised, first
+  // mapping pass done
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool ev_recorded = false;
 };
 
@@ -708,6 +710,7 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     LCH(launch_shoot_ipm(h->d_md.p, &h->md, 1, work, h->md.square_cells != 0, h->counter.p, h->err.p,
                         shoot_grid(), st));
   }
+  CKS(record(h, 5, st));
   LCH(launch_big_ipm(h->md, st));
   CKS(record(h, 3, st));
   LCH(launch_normalize(h->acc.p, h->span.p, P.npix, map_scale(P), h->map.p, st));
@@ -811,7 +814,7 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
 
   CK(cudaGetDevice(&h->device));
   CK(cudaStreamCreateWithFlags(&h->plan_stream, cudaStreamNonBlocking));
-  for (int k = 0; k < 5; k++) CK(cudaEventCreate(&h->ev[k]));
+  for (int k = 0; k < 6; k++) CK(cudaEventCreate(&h->ev[k]));
   cudaStream_t st = h->plan_stream;
 
   // stars to the device
@@ -924,6 +927,7 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
   lead->launches++;
   for (int i = 0; i < n; i++) {
     mm_map *h = hs[i];
+    CKS(record(h, 5, st));
     LCH(launch_big_ipm(h->md, st));
     CKS(record(h, 3, st));
     LCH(launch_normalize(h->acc.p, h->span.p, h->P.npix, map_scale(h->P), h->map.p, st));
@@ -1045,6 +1049,7 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
   out->rays = (h->col_hi - h->col_lo + 1) * (h->row_hi - h->row_lo + 1);
   out->cells = (h->col_hi - h->col_lo) * (h->row_hi - h->row_lo);
   out->ms_tree = out->ms_expansions = out->ms_shoot = out->ms_normalize = out->ms_total = -1.0;
+  out->ms_first_pass = out->ms_second_pass = -1.0;
   if (h->last_stream || h->ran) CK(cudaStreamSynchronize(h->last_stream));
   if (h->mode == MM_FMM_FP32 && h->n_nodes > 0) {
     std::vector<int32_t> fc(h->n_nodes);
@@ -1091,6 +1096,10 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
     }
     CK(cudaEventElapsedTime(&d, h->ev[2], h->ev[3]));
     out->ms_shoot = d;
+    CK(cudaEventElapsedTime(&d, h->ev[2], h->ev[5]));
+    out->ms_first_pass = d;
+    CK(cudaEventElapsedTime(&d, h->ev[5], h->ev[3]));
+    out->ms_second_pass = d;
     CK(cudaEventElapsedTime(&a, h->ev[3], h->ev[4]));
     out->ms_normalize = a;
   }
