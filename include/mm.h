@@ -91,7 +91,11 @@ typedef struct {
                                deflection, to land beyond the same map edge
                                as the row below (the map is unchanged: such
                                cells lie wholly outside it) */
-  int32_t reserved;
+  int32_t big_queue_slots;  /* queue for the second mapping pass, in triangles:
+                               0 -> 1 per 12 cells (2^16 .. 2^27); -1 -> none
+                               (the first pass deals every larger triangle);
+                               n > 0 -> n.  Batches that do not fit are dealt
+                               by the first pass (same map). */
 } mm_options;
 
 /* Every derived scalar of a run (host-side numbers; no GPU needed). */

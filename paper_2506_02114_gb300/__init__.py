@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
                 ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
                 ("rows_per_item", ctypes.c_int32), ("sub_levels", ctypes.c_int32),
                 ("col_begin", ctypes.c_int64), ("col_end", ctypes.c_int64),
-                ("no_cull", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("no_cull", ctypes.c_int32), ("big_queue_slots", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -165,7 +165,8 @@ def _ptr(a):
 
 def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=None,
                  flux_fraction_f=0.0, center_y=(0.0, 0.0), row_begin=0, row_end=0,
-                 rows_per_item=0, col_begin=0, col_end=0, sub_levels=0, cull=True):
+                 rows_per_item=0, col_begin=0, col_end=0, sub_levels=0, cull=True,
+                 big_queue_slots=0):
     o = Options()
     o.mode = int(mode)
     o.time_stages = 1 if time_stages else 0
@@ -179,6 +180,7 @@ def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=No
     o.rows_per_item = int(rows_per_item)
     o.sub_levels = int(sub_levels)
     o.no_cull = 0 if cull else 1
+    o.big_queue_slots = int(big_queue_slots)
     o.col_begin, o.col_end = int(col_begin), int(col_end)
     return o
 

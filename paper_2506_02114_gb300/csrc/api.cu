@@ -648,8 +648,12 @@ static mm_status alloc_map_buffers(mm_map *h) {
   // (48 B each); batches that do not fit are dealt out by the first kernel
   {
     const int64_t cells = (h->col_hi - h->col_lo) * (h->row_hi - h->row_lo);
-    h->bigq_cap = std::min<int64_t>(int64_t(1) << 27, std::max<int64_t>(int64_t(1) << 16, cells / 12));
-    CK(h->bigq.ensure((size_t)h->bigq_cap * MM_TRIJOB_BYTES));
+    const int32_t want = h->opt.big_queue_slots;
+    h->bigq_cap = want < 0 ? 0
+                  : want > 0 ? (int64_t)want
+                             : std::min<int64_t>(int64_t(1) << 27,
+                                                 std::max<int64_t>(int64_t(1) << 16, cells / 12));
+    if (h->bigq_cap > 0) CK(h->bigq.ensure((size_t)h->bigq_cap * MM_TRIJOB_BYTES));
     CK(h->bigq_n.ensure(2));
   }
   CK(h->err.ensure(1));
@@ -753,6 +757,8 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
     return fail(MM_EINVAL, "leaf_size %d outside [0, 1024]", leaf_size);
   if (h->opt.mode != MM_FMM_FP32 && h->opt.mode != MM_PLAIN_FP64)
     return fail(MM_EINVAL, "unknown mode %d", h->opt.mode);
+  if (h->opt.big_queue_slots < -1)
+    return fail(MM_EINVAL, "big_queue_slots %d below -1", h->opt.big_queue_slots);
   if (h->opt.sub_levels < -1 || h->opt.sub_levels > MM_SUB_MAX)
     return fail(MM_EINVAL, "sub_levels %d outside [-1, %d]", h->opt.sub_levels, MM_SUB_MAX);
   if (n_stars > 0 && !pos_xy) return fail(MM_EINVAL, "pos_xy is NULL");

@@ -232,3 +232,24 @@ def test_culling_leaves_the_map_unchanged():
               "triangles_rows", "triangles_dropped"):
         assert stats[0][k] == stats[1][k], k
     assert np.array_equal(fixed[0], fixed[1])
+
+
+@pytest.mark.parametrize("mode", [mm.MM_FMM_FP32, mm.MM_PLAIN_FP64])
+def test_second_pass_queue_sizes_leave_the_map_unchanged(mode):
+    """Larger triangles go through the device queue to the second mapping
+    pass; with no queue the first pass deals them all, and with a queue too
+    small for the map the batches that do not fit are dealt in place and
+    their reserved slots hold empty jobs.  The fixed-point map is the same
+    in all three cases."""
+    m, pos = small_field(23, 0.45, 0.3, 0.4, hl=1.5, npix=64, rpp=10.0, mass_fn=synthetic.EQUAL)
+    maps, stats = [], []
+    for slots in (0, -1, 700):
+        h = mm.create(0.45, 0.3, 0.4, m, pos, 1.5, 64, 10.0, fmm_order=20, flux_fraction_f=0.01,
+                      mode=mode, big_queue_slots=slots)
+        mm.run(h, 0)
+        maps.append(mm.get_map_fixed(h))
+        stats.append(mm.get_stats(h))
+        mm.destroy(h)
+    big = stats[0]["triangles_box"] + stats[0]["triangles_rows"]
+    assert big > 1400, big  # the 700-slot queue overflows
+    assert np.array_equal(maps[0], maps[1]) and np.array_equal(maps[0], maps[2])
