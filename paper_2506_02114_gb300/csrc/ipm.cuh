@@ -62,7 +62,7 @@ __device__ __forceinline__ float rcp_approx_f(float x) {
 // FP32 fraction carries 24 significant bits, so it is rounded at 2^-24 and
 // shifted: 32-bit conversions only (64-bit ones would run on the FP64 pipe).
 __device__ __forceinline__ unsigned long long frac_to_fixed(float f) {
-  f = fminf(fmaxf(f, 0.0f), 1.0f);
+  f = __saturatef(f);  // clamp to [0, 1] (NaN -> 0)
   return (unsigned long long)__float2uint_rn(f * 16777216.0f) << 8;
 }
 
@@ -395,7 +395,7 @@ __device__ __forceinline__ float edge_x_at(float y, float px, float py, float qx
 // formed from sub-interval lengths so that a nearly vertical piece loses no
 // precision; h times it is the piece's integral.
 __device__ __forceinline__ float piece_mean(float a, float b) {
-  const float w = fminf(fmaxf(a, 0.f), 1.f), v = fminf(fmaxf(b, 0.f), 1.f);
+  const float w = __saturatef(a), v = __saturatef(b);  // clamp to [0, 1]
   const float in = fmaf(0.5f * (v - w), v + w, fmaxf(b - fmaxf(a, 1.f), 0.f));
   const float len = b - a;
   return len > 0.f ? in * rcp_approx_f(len) : w;
