@@ -274,18 +274,21 @@ def run_native(args):
         m_pin = torch.from_numpy(np.ascontiguousarray(m)).pin_memory()
         pos_pin = torch.from_numpy(np.ascontiguousarray(pos)).pin_memory()
         out_pin = torch.empty((wl.npix, wl.npix), dtype=torch.float32).pin_memory()
-        e2e_times = []
+        e2e_times, parts = [], []
         for k in range(2 + max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             he = mm.create(wl.kappa, wl.gamma, wl.s, m_pin.numpy(), pos_pin.numpy(), wl.half_length,
                            wl.npix, wl.rays_per_pixel, fmm_order=wl.fmm_order)
+            ta = time.perf_counter()
             mm.run(he, stream.cuda_stream)
             mm.get_map(he, out_pin.numpy())
+            tb = time.perf_counter()
             mm.destroy(he)
             t1 = time.perf_counter()
             if k >= 2:
                 e2e_times.append(t1 - t0)
+                parts.append((ta - t0, tb - ta, t1 - tb))
         e2e_value = world * rays / float(np.mean(e2e_times))
         fp64_plain = {"value": plain_rays_s, "unit": UNIT, "rays": sp["rays"],
                       "sample": "%d cell rows, full width, same grid" % band,
@@ -293,7 +296,9 @@ def run_native(args):
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(m.nbytes + pos.nbytes),
                "d2h_bytes_per_step": int(wl.npix * wl.npix * 4),
-               "includes": "mm_create (stars H2D, plan) + mm_run + mm_get_map (D2H) + mm_destroy"}
+               "includes": "mm_create (stars H2D, plan) + mm_run + mm_get_map (D2H) + mm_destroy",
+               "ms_create_run_destroy": [round(1e3 * float(np.mean([p[q] for p in parts])), 3)
+                                         for q in range(3)]}
 
     # roofline of the hot kernel, the fused deflection + first mapping pass
     # (FP32 ALU bound); the second pass deals the queued larger triangles

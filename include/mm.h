@@ -26,6 +26,9 @@
  *     L = half_length, d = 2L/npix, c = map centre.
  *   - A handle owns all of its device memory and is used by one host thread
  *     at a time.  Different handles may run concurrently on different streams.
+ *     Its buffers come from the device's default memory pool (stream-ordered
+ *     allocation); the library raises that pool's release threshold, so the
+ *     memory of a destroyed handle stays with the process for the next one.
  *   - "stream" arguments are cudaStream_t values passed as void*; NULL is the
  *     legacy default stream.
  */

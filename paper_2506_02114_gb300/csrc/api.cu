@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -81,34 +82,74 @@ void set_last_error(const char *msg) { g_err = msg; }
 // device buffers
 // ---------------------------------------------------------------------------
 
+// stream on which DBuf allocates and frees (NULL: synchronous cudaMalloc/cudaFree)
+static thread_local cudaStream_t g_alloc_stream = nullptr;
+
 template <class T>
 struct DBuf {
   T *p = nullptr;
   size_t n = 0;
+  bool pooled = false;  // p came from cudaMallocAsync
   cudaError_t ensure(size_t count, bool keep = false) {
     if (count == 0) count = 1;
     if (count <= n) return cudaSuccess;
     T *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    const cudaStream_t s = g_alloc_stream;
+    cudaError_t e = s ? cudaMallocAsync(&q, count * sizeof(T), s) : cudaMalloc(&q, count * sizeof(T));
     if (e != cudaSuccess) return e;
     if (keep && p && n) {
-      e = cudaMemcpy(q, p, n * sizeof(T), cudaMemcpyDeviceToDevice);
+      e = s ? cudaMemcpyAsync(q, p, n * sizeof(T), cudaMemcpyDeviceToDevice, s)
+            : cudaMemcpy(q, p, n * sizeof(T), cudaMemcpyDeviceToDevice);
       if (e != cudaSuccess) {
-        cudaFree(q);
+        free_buf(q, s != nullptr);
         return e;
       }
     }
-    if (p) cudaFree(p);
+    if (p) free_buf(p, pooled);
     p = q;
     n = count;
+    pooled = s != nullptr;
     return cudaSuccess;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) free_buf(p, pooled);
     p = nullptr;
     n = 0;
+    pooled = false;
+  }
+  // stream-ordered free for pooled memory when an allocation stream is set;
+  // otherwise (or for cudaMalloc memory) a synchronous cudaFree
+  static void free_buf(T *q, bool from_pool) {
+    if (from_pool && g_alloc_stream)
+      cudaFreeAsync(q, g_alloc_stream);
+    else
+      cudaFree(q);
   }
 };
+
+// Buffers of a handle are allocated and freed in stream order on its plan
+// stream, from the device's default memory pool, whose release threshold is
+// raised so that the memory of a destroyed handle is reused by the next one
+// instead of being returned to the driver (creating and destroying handles
+// of the same size then costs no driver allocation).
+struct AllocStream {
+  cudaStream_t prev;
+  explicit AllocStream(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+  ~AllocStream() { g_alloc_stream = prev; }
+};
+
+static void keep_pool_memory(int dev) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t threshold = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  }
+  done[dev] = true;
+}
 
 // ---------------------------------------------------------------------------
 // the handle
@@ -820,6 +861,8 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
 
   CK(cudaGetDevice(&h->device));
   CK(cudaStreamCreateWithFlags(&h->plan_stream, cudaStreamNonBlocking));
+  keep_pool_memory(h->device);
+  AllocStream alloc_on(h->plan_stream);
   for (int k = 0; k < 6; k++) CK(cudaEventCreate(&h->ev[k]));
   cudaStream_t st = h->plan_stream;
 
@@ -1116,6 +1159,8 @@ void mm_destroy(mm_map *h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->last_stream) cudaStreamSynchronize(h->last_stream);
+  // frees in stream order on the plan stream (synchronised below)
+  AllocStream free_on(h->plan_stream);
   DBuf<double> *dbs[] = {&h->pos_in, &h->m_in, &h->sx, &h->sy, &h->sm};
   for (auto *b : dbs) b->release();
   h->keys_in.release();
@@ -1150,7 +1195,10 @@ void mm_destroy(mm_map *h) {
   h->batch_md.release();
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
-  if (h->plan_stream) cudaStreamDestroy(h->plan_stream);
+  if (h->plan_stream) {
+    cudaStreamSynchronize(h->plan_stream);
+    cudaStreamDestroy(h->plan_stream);
+  }
   delete h;
 }
 
