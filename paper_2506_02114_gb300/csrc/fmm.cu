@@ -298,11 +298,12 @@ __global__ void k_near_count(TreeDev T, FmmConst C, int64_t n_rec, const int32_t
 // NB >= p_eval bounds the coefficients at compile time, so they stay in
 // registers.
 template <int NB>
-__global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
+__global__ void __launch_bounds__(64) k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
                                 const int32_t *active_list, const int32_t *near_off,
                                 const int32_t *near_cnt, const double2 *__restrict__ loc,
                                 LeafRec *leaf, NearPos *near_pos, float *near_m, float2 *coef,
                                 unsigned *err) {
+  __shared__ float2 s_cf[64][MM_PMAX + 1];  // per thread: FP32 copy of the leaf's coefficients
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_rec) return;
   int64_t node;
@@ -321,28 +322,48 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
   R.cull_side = MM_CULL_NONE;
   R.cull_r2 = -1.f;
 
-  // re-centred leaf expansion, d_1 .. d_pe
-  double2 d[NB + 1];
+  // re-centred leaf expansion.  d_1 sets the FP64 image of the centre and is
+  // formed in FP64; d_2..d_pe are stored as FP32 coefficients, scaled to the
+  // sub-cell (terms decay like the convergence ratio), and are formed in
+  // FP32 from FP32 copies of the leaf's coefficients (GB300's FP64 rate is
+  // 1/64 of its FP32 rate).
   const double2 *c = loc + node * P1;
   const double ux = (cx - zx) / L, uy = (cy - zy) / L, r = Lq / L;
-  double rn = 1.0;
-#pragma unroll
-  for (int n = 1; n <= NB; n++) {
-    d[n] = make_double2(0.0, 0.0);
-    if (n > pe) continue;
-    rn *= r;
-    double sx = 0.0, sy = 0.0, px = 1.0, py = 0.0, binom = 1.0;  // u^(l-n), C(l, n)
-#pragma unroll 1
-    for (int l = n; l <= p; l++) {
+  double2 d1 = make_double2(0.0, 0.0);
+  if (pe >= 1) {
+    double sx = 0.0, sy = 0.0, px = 1.0, py = 0.0;  // u^(l-1); C(l, 1) = l
+    for (int l = 1; l <= p; l++) {
       const double2 cl = c[l];
-      sx += binom * (cl.x * px - cl.y * py);
-      sy += binom * (cl.x * py + cl.y * px);
+      sx += l * (cl.x * px - cl.y * py);
+      sy += l * (cl.x * py + cl.y * px);
       const double npx = px * ux - py * uy;
       py = px * uy + py * ux;
       px = npx;
-      binom = binom * (double)(l + 1) / (double)(l + 1 - n);
     }
-    d[n] = make_double2(sx * rn, sy * rn);
+    d1 = make_double2(sx * r, sy * r);
+  }
+  float2 *cf = s_cf[threadIdx.x];
+  for (int l = 0; l <= p; l++) cf[l] = make_float2((float)c[l].x, (float)c[l].y);
+  const float fux = (float)ux, fuy = (float)uy, fr = (float)r;
+  float2 d[NB + 1];
+  float rn = fr;
+#pragma unroll
+  for (int n = 2; n <= NB; n++) {
+    d[n] = make_float2(0.f, 0.f);
+    if (n > pe) continue;
+    rn *= fr;
+    float sx = 0.f, sy = 0.f, px = 1.f, py = 0.f, binom = 1.f;  // u^(l-n), C(l, n)
+#pragma unroll 1
+    for (int l = n; l <= p; l++) {
+      const float2 cl = cf[l];
+      sx = fmaf(binom, cl.x * px - cl.y * py, sx);
+      sy = fmaf(binom, cl.x * py + cl.y * px, sy);
+      const float npx = px * fux - py * fuy;
+      py = px * fuy + py * fux;
+      px = npx;
+      binom = binom * (float)(l + 1) / (float)(l + 1 - n);
+    }
+    d[n] = make_float2(sx * rn, sy * rn);
   }
 
   // near-field stars: direct (in this record's frame) or into the expansion;
@@ -368,19 +389,22 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
             m_direct += T.sm[i];
             k++;
           } else {
-            // 1/w = L_q / (z_i - z_q)
+            // 1/w = L_q / (z_i - z_q); d_1 in FP64, the rest in FP32
             const double den = dxs * dxs + dys * dys;
             const double ix = Lq * dxs / den, iy = -Lq * dys / den;
             const double m = T.sm[i];
-            double tx = ix, ty = iy;  // w^-n
+            d1.x -= m * ix;
+            d1.y -= m * iy;
+            const float fix = (float)ix, fiy = (float)iy, fm = (float)m;
+            float tx = fix * fix - fiy * fiy, ty = 2.f * fix * fiy;  // w^-2
 #pragma unroll
-            for (int n = 1; n <= NB; n++) {
+            for (int n = 2; n <= NB; n++) {
               if (n <= pe) {
-                d[n].x -= m * tx / n;
-                d[n].y -= m * ty / n;
+                d[n].x -= fm * tx / n;
+                d[n].y -= fm * ty / n;
               }
-              const double ntx = tx * ix - ty * iy;
-              ty = tx * iy + ty * ix;
+              const float ntx = tx * fix - ty * fiy;
+              ty = tx * fiy + ty * fix;
               tx = ntx;
             }
           }
@@ -391,14 +415,13 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
   R.near_cnt = (int32_t)(k - R.near_off);
 
   const double s = 1.0 / (Lq * C.delta);
+  const float fs = (float)s;
 #pragma unroll
   for (int n = 2; n <= NB; n++)
-    if (n <= pe)
-      coef[g * cs + (n - 2)] = make_float2((float)(n * d[n].x * s), (float)(n * d[n].y * s));
+    if (n <= pe) coef[g * cs + (n - 2)] = make_float2(n * d[n].x * fs, n * d[n].y * fs);
   for (int kk = pe - 1; kk < cs; kk++) coef[g * cs + kk] = make_float2(0.f, 0.f);
 
   // FP64 image of the sub-cell centre: macro model + sheet - far field there
-  const double2 d1 = pe >= 1 ? d[1] : make_double2(0.0, 0.0);
   const double ak = 1.0 - C.kappa + C.kappa_star;
   const double Wx = (ak + C.gamma) * cx - d1.x / Lq;
   const double Wy = (ak - C.gamma) * cy + d1.y / Lq;  // - conj(d1/L_q)
@@ -433,7 +456,7 @@ __global__ void k_leaf_finalize(TreeDev T, FmmConst C, int64_t n_rec,
 #pragma unroll
     for (int n = 2; n <= NB; n++) {
       zp *= zmax;  // zeta_max^(n-1)
-      if (n <= pe) F += hypot(n * d[n].x * s, n * d[n].y * s) * zp;
+      if (n <= pe) F += hypot((double)(n * d[n].x * fs), (double)(n * d[n].y * fs)) * zp;
     }
     F *= 1.01;
     const double Bu = fabs(ak + C.gamma) * (Lq + hmax) / C.delta + F;
