@@ -67,6 +67,9 @@ def parse_args():
                     help="override the workload's rays per pixel (smaller profiling cases)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the map steps only: no FP64 band, end-to-end or CPU legs")
+    ap.add_argument("--autotune", action="store_true",
+                    help="let mm_create choose leaf size, sub-cell levels and work-item rows "
+                         "by timing (mm_options.autotune; no cache file)")
     return ap.parse_args()
 
 
@@ -208,8 +211,11 @@ def run_native(args):
     m, pos = wl.stars()
     args_map = (wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, wl.npix, wl.rays_per_pixel)
     stream = torch.cuda.Stream(device=dev)
-    h = mm.create(*args_map, fmm_order=wl.fmm_order, time_stages=True)
+    h = mm.create(*args_map, fmm_order=wl.fmm_order, time_stages=True, autotune=args.autotune)
     st0 = mm.get_stats(h)
+    # the end-to-end leg creates its handles with the settings chosen here
+    tuned = (dict(leaf_size=st0["leaf_size"], sub_levels=st0["sub_levels"],
+                  rows_per_item=st0["rows_per_item"]) if args.autotune else {})
     rays = st0["rays"]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
@@ -279,7 +285,7 @@ def run_native(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             he = mm.create(wl.kappa, wl.gamma, wl.s, m_pin.numpy(), pos_pin.numpy(), wl.half_length,
-                           wl.npix, wl.rays_per_pixel, fmm_order=wl.fmm_order)
+                           wl.npix, wl.rays_per_pixel, fmm_order=wl.fmm_order, **tuned)
             ta = time.perf_counter()
             mm.run(he, stream.cuda_stream)
             mm.get_map(he, out_pin.numpy())
@@ -342,7 +348,8 @@ def run_native(args):
                    "half_length": wl.half_length, "rays_per_pixel": wl.rays_per_pixel,
                    "ray_grid": st["params"]["n"], "rays": rays, "fmm_order": p,
                    "eval_order": pe, "sub_levels": st["sub_levels"],
-                   "leaf_size": st["leaf_size"], "l2": "flushed before every step (256 MiB write)",
+                   "leaf_size": st["leaf_size"], "rows_per_item": st["rows_per_item"],
+                   "autotuned": st["autotuned"], "l2": "flushed before every step (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "maps_per_s": world / (ms_per_step * 1e-3),
         "stages_ms": {k: st[k] for k in ("ms_tree", "ms_expansions", "ms_shoot", "ms_first_pass",

@@ -99,6 +99,34 @@ typedef struct {
                                (the first pass deals every larger triangle);
                                n > 0 -> n.  Batches that do not fit are dealt
                                by the first pass (same map). */
+  int32_t autotune;         /* FMM mode, 1: mm_create first times candidate
+                               settings and keeps the fastest: leaf_size in
+                               {16, 32, 64} when its argument is 0, sub_levels in
+                               {1, 2} when 0, rows_per_item in {automatic, 64,
+                               512} when 0.  Each candidate plan covers the
+                               whole grid (or band) and shoots every k-th row
+                               block of work items (k <= 16, a uniform sample),
+                               scored as tree + expansions + k x mapping time,
+                               the best of two timed runs.  p is not tuned: when
+                               0 it stays the smallest order App. C.3's error
+                               rule allows (a larger p only adds work).  The
+                               choice changes the map only within the FMM
+                               tolerances (leaf_size, sub_levels) and not at all
+                               through rows_per_item.  Ignored in
+                               MM_PLAIN_FP64 mode and when nothing is left 0. */
+  int32_t reserved0;        /* 0 */
+  const char *tune_cache;   /* autotune: path of a JSON-lines file of earlier
+                               choices (NULL: none), read first and appended
+                               to after a timed choice.  One object per line:
+                               {"key": K, "leaf_size": L, "sub_levels": S,
+                               "rows_per_item": R, "ms_estimate": T}, K built
+                               from the GPU's compute capability, the requested
+                               fmm_order, leaf_size, sub_levels and
+                               rows_per_item, and floor(log2) of N_star, the
+                               rays and npix; the last matching line wins.
+                               Unreadable files and malformed lines are
+                               ignored; a failed write is not an error.  Read
+                               only during mm_create. */
 } mm_options;
 
 /* Every derived scalar of a run (host-side numbers; no GPU needed). */
@@ -155,6 +183,10 @@ typedef struct {
      triangles) + ms_second_pass (the queued larger triangles) */
   double ms_tree, ms_expansions, ms_shoot, ms_normalize, ms_total;
   double ms_first_pass, ms_second_pass;
+  int32_t rows_per_item;    /* rows of cells per work item in use */
+  int32_t autotuned;        /* 0: not tuned; 1: tuned by timing; 2: taken from
+                               the tune_cache file */
+  double ms_autotune;       /* host wall time mm_create spent tuning, 0 if none */
 } mm_stats;
 
 /*

@@ -12,6 +12,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -226,6 +227,10 @@ struct mm_map {
   // mapping pass done
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool ev_recorded = false;
+
+  // autotuner outcome (mm_stats.autotuned, ms_autotune)
+  int tuned = 0;
+  double ms_tune = 0.0;
 };
 
 // ---------------------------------------------------------------------------
@@ -627,6 +632,7 @@ static void fill_mapdev(mm_map *h) {
   }
   M.rows_per_item = h->rows_per_item;
   M.row_blocks = (h->row_hi - h->row_lo + h->rows_per_item - 1) / h->rows_per_item;
+  M.item_stride = 1;
   M.work_begin = 0;
   M.col_cell = h->col_cell.p;
   M.row_cell = h->row_cell.p;
@@ -751,7 +757,8 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
       CKS(prepare(h, st));
     }
     CKS(record(h, 2, st));
-    const int64_t work = (int64_t)h->md.strips * h->md.row_blocks;
+    const int64_t work =
+        (int64_t)h->md.strips * ((h->md.row_blocks + h->md.item_stride - 1) / h->md.item_stride);
     LCH(launch_shoot_ipm(h->d_md.p, &h->md, 1, work, h->md.square_cells != 0, h->counter.p, h->err.p,
                         shoot_grid(), st));
   }
@@ -908,6 +915,203 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
   return MM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: the settings that change the speed of a map but not what it
+// computes (beyond the FMM tolerances), chosen by timing candidate plans.
+// ---------------------------------------------------------------------------
+
+struct TuneChoice {
+  int32_t leaf = 32, sub = 0, rpi = 0;
+};
+
+static bool tune_valid(const TuneChoice &c) {
+  return c.leaf >= 1 && c.leaf <= 1024 && c.sub >= -1 && c.sub <= MM_SUB_MAX && c.rpi >= 0 &&
+         c.rpi <= 4096;
+}
+
+static int log2_bucket(double v) { return v >= 1.0 ? (int)std::floor(std::log2(v)) : 0; }
+
+static std::string tune_key(int dev, const mm_options &o, int32_t fmm_order, int32_t leaf_size,
+                            int64_t n_stars, const mm_params &P) {
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  char b[256];
+  snprintf(b, sizeof b, "sm_%d%d/p%d/leaf%d/sub%d/rpi%d/nstar%d/rays%d/npix%d", major, minor,
+           fmm_order, leaf_size, o.sub_levels, o.rows_per_item, log2_bucket((double)n_stars),
+           log2_bucket((double)P.n[0] * (double)P.n[1]), log2_bucket((double)P.npix));
+  return b;
+}
+
+// integer value of "name": in one line of the cache
+static bool json_int(const std::string &line, const char *name, int32_t &v) {
+  const std::string pat = std::string("\"") + name + "\":";
+  size_t k = line.find(pat);
+  if (k == std::string::npos) return false;
+  k += pat.size();
+  while (k < line.size() && line[k] == ' ') k++;
+  const char *s = line.c_str() + k;
+  char *end = nullptr;
+  const long x = strtol(s, &end, 10);
+  if (end == s || x < -2147483647L || x > 2147483647L) return false;
+  v = (int32_t)x;
+  return true;
+}
+
+static bool tune_cache_lookup(const char *path, const std::string &key, TuneChoice &out) {
+  if (!path) return false;
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  const std::string want = "\"key\": \"" + key + "\"";
+  bool found = false;
+  char buf[1024];
+  while (fgets(buf, sizeof buf, f)) {
+    const std::string line(buf);
+    if (line.find(want) == std::string::npos) continue;
+    TuneChoice c;
+    if (json_int(line, "leaf_size", c.leaf) && json_int(line, "sub_levels", c.sub) &&
+        json_int(line, "rows_per_item", c.rpi) && tune_valid(c)) {
+      out = c;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+static void tune_cache_store(const char *path, const std::string &key, const TuneChoice &c,
+                             double ms) {
+  if (!path) return;
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f,
+          "{\"key\": \"%s\", \"leaf_size\": %d, \"sub_levels\": %d, \"rows_per_item\": %d, "
+          "\"ms_estimate\": %.4f}\n",
+          key.c_str(), c.leaf, c.sub, c.rpi, ms);
+  fclose(f);
+}
+
+struct CreateArgs {
+  double kappa, gamma, s;
+  int64_t n_stars;
+  const double *masses, *pos_xy;
+  double half_length;
+  int32_t npix;
+  double rays_per_pixel;
+  int32_t fmm_order;
+};
+
+// Device time of one sampled run of a trial handle, scaled to the whole grid:
+// tree + expansions + stride x mapping + normalisation.
+static mm_status trial_ms(mm_map *t, double scale, double &ms) {
+  CKS(run_one(t, t->plan_stream));
+  CK(cudaStreamSynchronize(t->plan_stream));
+  unsigned e = 0;
+  CK(cudaMemcpy(&e, t->err.p, sizeof e, cudaMemcpyDeviceToHost));
+  if (e) return fail(MM_ECUDA, "internal: autotune trial run reported error 0x%x", e);
+  float a = 0.f, b = 0.f, c = 0.f;
+  CK(cudaEventElapsedTime(&a, t->ev[0], t->ev[2]));
+  CK(cudaEventElapsedTime(&b, t->ev[2], t->ev[3]));
+  CK(cudaEventElapsedTime(&c, t->ev[3], t->ev[4]));
+  ms = (double)a + scale * (double)b + (double)c;
+  return MM_OK;
+}
+
+// Times every candidate (leaf_size x sub_levels x rows_per_item over the
+// settings left 0) and writes the fastest into o / leaf_size.
+static mm_status autotune(const CreateArgs &a, mm_options &o, int32_t &leaf_size, int &tuned,
+                          double &ms_tune) {
+  tuned = 0;
+  ms_tune = 0.0;
+  if (!o.autotune || o.mode != MM_FMM_FP32) return MM_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<int32_t> leafs = {leaf_size}, subs = {o.sub_levels}, rpis = {o.rows_per_item};
+  if (leaf_size == 0) leafs = {16, 32, 64};
+  if (o.sub_levels == 0) subs = {1, 2};
+  if (o.rows_per_item == 0) rpis = {0, 64, 512};
+  if (leafs.size() * subs.size() * rpis.size() == 1) return MM_OK;
+  mm_params P;
+  CKS(derive(a.kappa, a.gamma, a.s, a.n_stars, a.masses, a.half_length, a.npix,
+             a.rays_per_pixel, o, P));
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const std::string key = tune_key(dev, o, a.fmm_order, leaf_size, a.n_stars, P);
+  TuneChoice best;
+  if (tune_cache_lookup(o.tune_cache, key, best)) {
+    tuned = 2;
+  } else {
+    double best_ms = 1e300;
+    bool any = false;
+    mm_status last = MM_OK;
+    std::string last_msg;
+    for (int32_t leaf : leafs)
+      for (int32_t sub : subs) {
+        mm_map *t = new (std::nothrow) mm_map();
+        if (!t) return fail(MM_ENOMEM, "host allocation failed");
+        t->opt = o;
+        t->opt.autotune = 0;
+        t->opt.tune_cache = nullptr;
+        t->opt.time_stages = 1;
+        t->opt.sub_levels = sub;
+        t->opt.rows_per_item = 0;
+        mm_status s = create_impl(t, a.kappa, a.gamma, a.s, a.n_stars, a.masses, a.pos_xy,
+                                  a.half_length, a.npix, a.rays_per_pixel, a.fmm_order, leaf);
+        for (size_t r = 0; s == MM_OK && r < rpis.size(); r++) {
+          t->opt.rows_per_item = rpis[r];
+          t->rows_per_item = rpis[r] > 0 ? std::min(rpis[r], 4096) : 256;
+          fill_mapdev(t);
+          // every k-th row block: >= 4 work items per resident warp remain
+          const int64_t items = (int64_t)t->md.strips * t->md.row_blocks;
+          const int64_t k = std::max<int64_t>(
+              1, std::min<int64_t>(16, items / (4 * 8 * (int64_t)shoot_grid())));
+          t->md.item_stride = k;
+          const int64_t sampled = (t->md.row_blocks + k - 1) / k;
+          const double scale = (double)t->md.row_blocks / (double)sampled;
+          cudaError_t ce = cudaMemcpy(t->d_md.p, &t->md, sizeof(MapDev), cudaMemcpyHostToDevice);
+          if (ce != cudaSuccess) {
+            s = fail(MM_ECUDA, "autotune: %s", cudaGetErrorString(ce));
+            break;
+          }
+          double est = 1e300;
+          for (int rep = 0; s == MM_OK && rep < 3; rep++) {
+            double ms = 0.0;
+            s = trial_ms(t, scale, ms);
+            if (rep > 0) est = std::min(est, ms);  // the first run is a warm-up
+          }
+          if (s == MM_OK && est < best_ms) {
+            best_ms = est;
+            best.leaf = leaf;
+            best.sub = sub;
+            best.rpi = rpis[r];
+            any = true;
+          }
+        }
+        if (s != MM_OK) {
+          last = s;
+          last_msg = g_err;
+        }
+        mm_destroy(t);
+        if (s == MM_ETIMEOUT || s == MM_ECUDA) {
+          g_err = last_msg;
+          return s;  // a device error is not a candidate's property
+        }
+      }
+    if (!any) {
+      g_err = last_msg;
+      return last != MM_OK ? last : fail(MM_ESTATE, "autotune: no candidate ran");
+    }
+    g_err.clear();
+    tuned = 1;
+    tune_cache_store(o.tune_cache, key, best, best_ms);
+  }
+  leaf_size = best.leaf;
+  o.sub_levels = best.sub;
+  o.rows_per_item = best.rpi;
+  ms_tune = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                .count();
+  return MM_OK;
+}
+
 mm_status mm_create(double kappa_tot, double shear, double smooth_fraction, int64_t n_stars,
                     const double *masses, const double *pos_xy, double half_length,
                     int32_t npix, double rays_per_pixel, int32_t fmm_order, int32_t leaf_size,
@@ -917,8 +1121,19 @@ mm_status mm_create(double kappa_tot, double shear, double smooth_fraction, int6
   mm_map *h = new (std::nothrow) mm_map();
   if (!h) return fail(MM_ENOMEM, "host allocation failed");
   if (opt) h->opt = *opt;
-  mm_status s = create_impl(h, kappa_tot, shear, smooth_fraction, n_stars, masses, pos_xy,
-                            half_length, npix, rays_per_pixel, fmm_order, leaf_size);
+  const CreateArgs args = {kappa_tot, shear,        smooth_fraction, n_stars,  masses, pos_xy,
+                           half_length, npix, rays_per_pixel,  fmm_order};
+  mm_status s = MM_OK;
+  if (h->opt.autotune && (leaf_size < 0 || leaf_size > 1024 || fmm_order < 0 ||
+                          fmm_order > MM_PMAX || h->opt.sub_levels < -1 ||
+                          h->opt.sub_levels > MM_SUB_MAX))
+    h->opt.autotune = 0;  // create_impl reports the invalid argument
+  if (h->opt.autotune) s = autotune(args, h->opt, leaf_size, h->tuned, h->ms_tune);
+  h->opt.autotune = 0;
+  h->opt.tune_cache = nullptr;
+  if (s == MM_OK)
+    s = create_impl(h, kappa_tot, shear, smooth_fraction, n_stars, masses, pos_xy, half_length,
+                    npix, rays_per_pixel, fmm_order, leaf_size);
   if (s != MM_OK) {
     std::string msg = g_err;
     mm_destroy(h);
@@ -1133,6 +1348,9 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
     out->rows_culled = (int64_t)st[6];
   }
   out->kernel_launches = h->launches;
+  out->rows_per_item = h->rows_per_item;
+  out->autotuned = h->tuned;
+  out->ms_autotune = h->ms_tune;
   if (h->ev_recorded) {
     float a = 0, b = 0, c = 0, d = 0;
     CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[4]));

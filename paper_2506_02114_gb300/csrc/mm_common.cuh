@@ -77,6 +77,8 @@ struct MapDev {
   int64_t col_begin, col_end; // cell columns [col_begin, col_end)
   int32_t strips, rows_per_item;
   int64_t row_blocks;
+  int64_t item_stride;        // >= 1: work item k covers row block k * item_stride
+                              // (> 1 only for the autotuner's sampled runs)
   int64_t work_begin;         // first global work item of this map
   // leaf lookup
   const int32_t *col_cell, *row_cell;   // finest-level cell index per vertex column / row

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
       last_map = mi;
     }
     const int64_t local = (int64_t)w - M.work_begin;
-    const int64_t s = local % M.strips, b = local / M.strips;
+    const int64_t s = local % M.strips, b = (local / M.strips) * M.item_stride;
     const int64_t i = M.col_begin + s * MM_STRIP + lane;
     const int64_t jb = M.row_begin + b * M.rows_per_item;
     int64_t je = jb + M.rows_per_item;

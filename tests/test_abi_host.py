@@ -93,3 +93,37 @@ def test_no_gpu_fails_loudly():
     with pytest.raises(mm.MMError) as e:
         mm.create(0.3, 0.1, 0.0, m, pos, 1.0, 16, img_half=(2.0, 2.0), ray_grid=(8, 8))
     assert e.value.status in (mm.MM_ECUDA, mm.MM_ENOMEM)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of mm_options, mm_params and mm_stats have the C
+    structs' size and every field's offset (gcc compiles a probe of mm.h)."""
+    import ctypes
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"mm_options": mm.Options, "mm_params": mm.Params, "mm_stats": mm.Stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "mm.h"', "int main(void) {"]
+    want = []
+    for cname, cls in structs.items():
+        lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        want.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, fname))
+            want.append(getattr(cls, fname).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.check_call([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == want
+
+
+def test_autotune_options_reach_the_structure():
+    o = mm.make_options(autotune=True, tune_cache="tune.jsonl")
+    assert o.autotune == 1 and o.tune_cache == b"tune.jsonl"
+    o = mm.make_options()
+    assert o.autotune == 0 and o.tune_cache is None
