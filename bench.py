@@ -354,6 +354,9 @@ def run_native(args):
         "maps_per_s": world / (ms_per_step * 1e-3),
         "stages_ms": {k: st[k] for k in ("ms_tree", "ms_expansions", "ms_shoot", "ms_first_pass",
                                          "ms_second_pass", "ms_normalize", "ms_total")},
+        "triangles": {k[len("triangles_"):]: st[k] for k in (
+            "triangles_clipped", "triangles_line", "triangles_quad", "triangles_box",
+            "triangles_rows", "triangles_dropped", "triangles_near_critical")},
         "fp64_plain": fp64_plain,
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -95,9 +95,15 @@ typedef struct {
                                as the row below (the map is unchanged: such
                                cells lie wholly outside it) */
   int32_t big_queue_slots;  /* queue for the second mapping pass, in triangles:
-                               0 -> 1 per 12 cells (2^16 .. 2^27); -1 -> none
-                               (the first pass deals every larger triangle);
-                               n > 0 -> n.  Batches that do not fit are dealt
+                               0 -> 1 per 12 cells (2^16 .. 2^27) when the
+                               map's accumulators (16 B per pixel) fit half
+                               the GPU's L2, else none; -1 -> none (the first
+                               pass deals every larger triangle); n > 0 -> n.
+                               With a queue and a map that fits, the first
+                               pass runs in consecutive segments of work
+                               items, each followed by the second pass, so
+                               that about one larger triangle per 12 cells
+                               fits.  Batches that still do not fit are dealt
                                by the first pass (same map). */
   int32_t autotune;         /* FMM mode, 1: mm_create first times candidate
                                settings and keeps the fastest: leaf_size in
@@ -127,6 +133,9 @@ typedef struct {
                                Unreadable files and malformed lines are
                                ignored; a failed write is not an error.  Read
                                only during mm_create. */
+  double critical_mu;       /* statistics: a mapped triangle whose local |mu|
+                               (image area / source area) exceeds this counts
+                               as near-critical (mm_stats); 0 -> 1e3 */
 } mm_options;
 
 /* Every derived scalar of a run (host-side numbers; no GPU needed). */
@@ -187,6 +196,8 @@ typedef struct {
   int32_t autotuned;        /* 0: not tuned; 1: tuned by timing; 2: taken from
                                the tune_cache file */
   double ms_autotune;       /* host wall time mm_create spent tuning, 0 if none */
+  int64_t triangles_near_critical; /* triangles not wholly beyond one map edge
+                               with local |mu| above critical_mu (last run) */
 } mm_stats;
 
 /*

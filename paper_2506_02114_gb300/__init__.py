@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
                 ("col_begin", ctypes.c_int64), ("col_end", ctypes.c_int64),
                 ("no_cull", ctypes.c_int32), ("big_queue_slots", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("tune_cache", ctypes.c_char_p)]
+                ("tune_cache", ctypes.c_char_p), ("critical_mu", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -82,7 +82,7 @@ class Stats(ctypes.Structure):
                 ("ms_normalize", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_first_pass", ctypes.c_double), ("ms_second_pass", ctypes.c_double),
                 ("rows_per_item", ctypes.c_int32), ("autotuned", ctypes.c_int32),
-                ("ms_autotune", ctypes.c_double)]
+                ("ms_autotune", ctypes.c_double), ("triangles_near_critical", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "params"}
@@ -170,7 +170,7 @@ def _ptr(a):
 def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=None,
                  flux_fraction_f=0.0, center_y=(0.0, 0.0), row_begin=0, row_end=0,
                  rows_per_item=0, col_begin=0, col_end=0, sub_levels=0, cull=True,
-                 big_queue_slots=0, autotune=False, tune_cache=None):
+                 big_queue_slots=0, autotune=False, tune_cache=None, critical_mu=0.0):
     o = Options()
     o.mode = int(mode)
     o.time_stages = 1 if time_stages else 0
@@ -187,6 +187,7 @@ def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=No
     o.big_queue_slots = int(big_queue_slots)
     o.col_begin, o.col_end = int(col_begin), int(col_end)
     o.autotune = 1 if autotune else 0
+    o.critical_mu = float(critical_mu)
     # (the structure keeps the encoded path alive while it lives)
     o.tune_cache = os.fsencode(tune_cache) if tune_cache is not None else None
     return o

@@ -231,6 +231,14 @@ struct mm_map {
   // autotuner outcome (mm_stats.autotuned, ms_autotune)
   int tuned = 0;
   double ms_tune = 0.0;
+
+  // The first mapping pass runs in `segments` launches over consecutive work
+  // items, each followed by the second pass, so that the queue of larger
+  // triangles (about one per 12 cells) fits its capacity.  Per segment k,
+  // seg_ev[2k] marks the end of its first pass and seg_ev[2k + 1] the end of
+  // its second (time_stages only).
+  int64_t segments = 1, last_segments = 0;
+  std::vector<cudaEvent_t> seg_ev;
 };
 
 // ---------------------------------------------------------------------------
@@ -660,6 +668,9 @@ static void fill_mapdev(mm_map *h) {
   M.sx = (float)(1.0 / (P.h[0] * P.delta));
   M.sy = (float)(P.h[1] / (P.h[0] * P.h[0] * P.delta));
   M.rho = (float)((P.h[1] / P.h[0]) * (P.h[1] / P.h[0]));
+  // twice the image triangle's area in pixel units, over the threshold |mu|
+  M.crit_area2 = (float)(P.h[0] * P.h[1] / (P.delta * P.delta) /
+                         (h->opt.critical_mu > 0.0 ? h->opt.critical_mu : 1e3));
   M.npix = P.npix;
   M.acc = h->acc.p;
   M.span = h->span.p;
@@ -691,17 +702,38 @@ static mm_status alloc_map_buffers(mm_map *h) {
   CK(h->map.ensure(np));
   CK(h->stat.ensure(8));
   CK(h->counter.ensure(1));
-  // queue for the second IPM pass: 1 slot per 12 cells, 2^16 .. 2^27 slots
-  // (48 B each); batches that do not fit are dealt out by the first kernel
+  // Queue for the second IPM pass.  It pays while the map's accumulators
+  // (acc + row-difference array, 16 B per pixel) stay in L2: the second pass
+  // then finds their lines there.  A larger map's lines are gone by the time
+  // the second pass reaches a triangle, whereas the first pass deals it where
+  // the lines are hot (measured on 5000^2 and 10000^2 maps: no queue was 18 %
+  // and 8 % faster than a queue, and first passes split into segments to fit
+  // the queue were 17-44 % slower).  Default: 1 slot per 12 cells, 2^16 ..
+  // 2^27 slots (48 B each), for maps that fit half the L2, else none.
+  // Batches that do not fit are dealt out by the first kernel.
   {
     const int64_t cells = (h->col_hi - h->col_lo) * (h->row_hi - h->row_lo);
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
+    const bool fits_l2 = 16.0 * (double)h->P.npix * (double)h->P.npix <= 0.5 * (double)l2;
     const int32_t want = h->opt.big_queue_slots;
     h->bigq_cap = want < 0 ? 0
                   : want > 0 ? (int64_t)want
-                             : std::min<int64_t>(int64_t(1) << 27,
-                                                 std::max<int64_t>(int64_t(1) << 16, cells / 12));
+                  : fits_l2  ? std::min<int64_t>(int64_t(1) << 27,
+                                                 std::max<int64_t>(int64_t(1) << 16, cells / 12))
+                             : 0;
     if (h->bigq_cap > 0) CK(h->bigq.ensure((size_t)h->bigq_cap * MM_TRIJOB_BYTES));
     CK(h->bigq_n.ensure(2));
+    // a map that fits: the first pass runs in segments so that each
+    // segment's larger triangles (about one per 12 cells) fit the queue
+    h->segments = 1;
+    if (h->bigq_cap > 0 && h->mode == MM_FMM_FP32 && fits_l2)
+      h->segments = std::max<int64_t>(1, (cells / 12 + h->bigq_cap - 1) / h->bigq_cap);
+    if (h->opt.time_stages && (int64_t)h->seg_ev.size() < 2 * h->segments) {
+      const size_t have = h->seg_ev.size();
+      h->seg_ev.resize(2 * h->segments, nullptr);
+      for (size_t k = have; k < h->seg_ev.size(); k++) CK(cudaEventCreate(&h->seg_ev[k]));
+    }
   }
   CK(h->err.ensure(1));
   CK(cudaMemset(h->err.p, 0, sizeof(unsigned)));  // read after the plan in every mode
@@ -747,6 +779,8 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
                                  st));
     LCH(launch_ipm_vertices(h->d_md.p, h->verts.p, h->col_hi - h->col_lo + 1, h->row_lo,
                             h->row_hi, h->counter.p, h->err.p, shoot_grid(), st));
+    CKS(record(h, 5, st));
+    LCH(launch_big_ipm(h->md, st));
   } else {
     // The plan of mm_create ran the whole tree and expansion pipeline on the
     // same stars; the first run uses that result instead of repeating it.
@@ -759,11 +793,25 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     CKS(record(h, 2, st));
     const int64_t work =
         (int64_t)h->md.strips * ((h->md.row_blocks + h->md.item_stride - 1) / h->md.item_stride);
-    LCH(launch_shoot_ipm(h->d_md.p, &h->md, 1, work, h->md.square_cells != 0, h->counter.p, h->err.p,
-                        shoot_grid(), st));
+    const int64_t nseg = std::max<int64_t>(1, std::min(h->segments, work));
+    const int64_t per = (work + nseg - 1) / nseg;
+    int64_t k = 0;
+    for (int64_t w0 = 0; w0 < work; w0 += per, k++) {
+      if (w0 > 0) {  // the previous segment's second pass has drained the queue
+        CK(cudaMemsetAsync(h->counter.p, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(h->bigq_n.p, 0, 2 * sizeof(unsigned long long), st));
+      }
+      MapDev ms = h->md;
+      ms.work_begin = -w0;  // this launch's item w is item w0 + w of the map
+      LCH(launch_shoot_ipm(h->d_md.p, &ms, 1, std::min(per, work - w0), h->md.square_cells != 0,
+                          h->counter.p, h->err.p, shoot_grid(), st));
+      if (h->opt.time_stages) CK(cudaEventRecord(h->seg_ev[2 * k], st));
+      LCH(launch_big_ipm(ms, st));
+      if (h->opt.time_stages) CK(cudaEventRecord(h->seg_ev[2 * k + 1], st));
+    }
+    h->last_segments = k;
+    CKS(record(h, 5, st));
   }
-  CKS(record(h, 5, st));
-  LCH(launch_big_ipm(h->md, st));
   CKS(record(h, 3, st));
   LCH(launch_normalize(h->acc.p, h->span.p, P.npix, map_scale(P), h->map.p, st));
   CKS(record(h, 4, st));
@@ -805,6 +853,8 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
     return fail(MM_EINVAL, "leaf_size %d outside [0, 1024]", leaf_size);
   if (h->opt.mode != MM_FMM_FP32 && h->opt.mode != MM_PLAIN_FP64)
     return fail(MM_EINVAL, "unknown mode %d", h->opt.mode);
+  if (!(h->opt.critical_mu >= 0.0) || !std::isfinite(h->opt.critical_mu))
+    return fail(MM_EINVAL, "critical_mu %g is negative or not finite", h->opt.critical_mu);
   if (h->opt.big_queue_slots < -1)
     return fail(MM_EINVAL, "big_queue_slots %d below -1", h->opt.big_queue_slots);
   if (h->opt.sub_levels < -1 || h->opt.sub_levels > MM_SUB_MAX)
@@ -1191,6 +1241,7 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
   lead->launches++;
   for (int i = 0; i < n; i++) {
     mm_map *h = hs[i];
+    h->last_segments = 0;  // one first pass for the whole batch
     CKS(record(h, 5, st));
     LCH(launch_big_ipm(h->md, st));
     CKS(record(h, 3, st));
@@ -1346,6 +1397,7 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
     out->triangles_rows = (int64_t)st[4];
     out->triangles_line = (int64_t)st[5];
     out->rows_culled = (int64_t)st[6];
+    out->triangles_near_critical = (int64_t)st[7];
   }
   out->kernel_launches = h->launches;
   out->rows_per_item = h->rows_per_item;
@@ -1363,10 +1415,22 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
     }
     CK(cudaEventElapsedTime(&d, h->ev[2], h->ev[3]));
     out->ms_shoot = d;
-    CK(cudaEventElapsedTime(&d, h->ev[2], h->ev[5]));
-    out->ms_first_pass = d;
-    CK(cudaEventElapsedTime(&d, h->ev[5], h->ev[3]));
-    out->ms_second_pass = d;
+    if (h->mode == MM_FMM_FP32 && h->last_segments > 0) {
+      double f = 0.0, g = 0.0;
+      for (int64_t k = 0; k < h->last_segments; k++) {
+        CK(cudaEventElapsedTime(&d, k ? h->seg_ev[2 * k - 1] : h->ev[2], h->seg_ev[2 * k]));
+        f += d;
+        CK(cudaEventElapsedTime(&d, h->seg_ev[2 * k], h->seg_ev[2 * k + 1]));
+        g += d;
+      }
+      out->ms_first_pass = f;
+      out->ms_second_pass = g;
+    } else {
+      CK(cudaEventElapsedTime(&d, h->ev[2], h->ev[5]));
+      out->ms_first_pass = d;
+      CK(cudaEventElapsedTime(&d, h->ev[5], h->ev[3]));
+      out->ms_second_pass = d;
+    }
     CK(cudaEventElapsedTime(&a, h->ev[3], h->ev[4]));
     out->ms_normalize = a;
   }
@@ -1412,6 +1476,8 @@ void mm_destroy(mm_map *h) {
   h->verts.release();
   h->batch_md.release();
   for (auto &e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto &e : h->seg_ev)
     if (e) cudaEventDestroy(e);
   if (h->plan_stream) {
     cudaStreamSynchronize(h->plan_stream);

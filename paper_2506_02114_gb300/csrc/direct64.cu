@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
   const int64_t rows = row_hi - row_lo;  // cell rows
   const int64_t rpi = M.rows_per_item;
   const int64_t total = strips * ((rows + rpi - 1) / rpi);
-  IpmCounters cnt = {0, 0, 0, 0, 0, 0, 0};
+  IpmCounters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   while (true) {
     unsigned long long w = 0;
     if (lane == 0) w = atomicAdd(work_counter, 1ull);
@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
     wq_drain(M, wq, lane);
     jq_share(M, jq, true, lane);
   }
-  unsigned v[MM_N_COUNTERS] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip,
-                               cnt.big,     cnt.line,    cnt.culled};
+  unsigned v[MM_N_COUNTERS] = {cnt.dropped, cnt.clipped, cnt.small,  cnt.strip,
+                               cnt.big,     cnt.line,    cnt.culled, cnt.critical};
 #pragma unroll
   for (int k = 0; k < MM_N_COUNTERS; k++) {
     for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);

@@ -237,9 +237,9 @@ __device__ __forceinline__ void wq_drain(const MapDev &M, WarpQueue &wq, int lan
 // crossing both grid lines, [3] box of at most MM_MED_PIXELS pixels (pixel
 // jobs), [4] larger (row jobs), [5] two pixels split by one grid line, [6]
 // vertex rows not computed because culling proved them beyond the map.
-#define MM_N_COUNTERS 7
+#define MM_N_COUNTERS 8
 struct IpmCounters {
-  unsigned dropped, clipped, small, strip, big, line, culled;
+  unsigned dropped, clipped, small, strip, big, line, culled, critical;
 };
 
 // A triangle shared out to the whole warp: frame pixel, frame coordinates,
@@ -286,6 +286,8 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     cnt.dropped++;
     return TRI_DONE;
   }
+  // near-critical: local |mu| = image area / source area above the threshold
+  cnt.critical += fabsf(area2) < M.crit_area2;
   if (a.px == b.px && a.px == c.px && a.py == b.py && a.py == c.py) {
     // all three vertices in one (closed) map pixel: all of the area is there
     run_add(M, ra, (long long)oy * M.npix + ox, MM_FIX_ONE);

@@ -100,6 +100,8 @@ struct MapDev {
   float A1, A2;               // (1 - kappa + kappa_star +- gamma) h / delta
   float sx, sy;               // 1/(h_x delta), h_y/(h_x^2 delta)
   float rho;                  // (h_y/h_x)^2
+  float crit_area2;           // 2 x source triangle area (px^2) below which the
+                              // triangle counts as near-critical
   // map
   int32_t npix;
   unsigned long long *acc;    // npix*npix fixed point, 2^32 = one triangle

@@ -231,14 +231,14 @@ __device__ __forceinline__ Vtx shfl_down_vtx(const Vtx &v, int d) {
 
 // Warp-reduce the per-lane triangle counters into the map's statistics.
 __device__ __forceinline__ void flush_counters(const MapDev &M, IpmCounters &cnt, int lane) {
-  unsigned v[MM_N_COUNTERS] = {cnt.dropped, cnt.clipped, cnt.small, cnt.strip,
-                               cnt.big,     cnt.line,    cnt.culled};
+  unsigned v[MM_N_COUNTERS] = {cnt.dropped, cnt.clipped, cnt.small,  cnt.strip,
+                               cnt.big,     cnt.line,    cnt.culled, cnt.critical};
 #pragma unroll
   for (int k = 0; k < MM_N_COUNTERS; k++) {
     for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);
     if (lane == 0 && v[k]) atomicAdd(&M.stat[k], (unsigned long long)v[k]);
   }
-  cnt = IpmCounters{0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  cnt = IpmCounters{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 }
 
 // Persistent warps; each work item is a strip of 31 cell columns by
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
   WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
   WarpQueue wq = {ws->quad, 0};
   JobQueue jq = {ws->big, &ws->rows, 0};
-  IpmCounters cnt = {0, 0, 0, 0, 0, 0, 0};
+  IpmCounters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   int last_map = -1;
   while (true) {
     unsigned long long w = 0;

@@ -237,13 +237,14 @@ def test_culling_leaves_the_map_unchanged():
 @pytest.mark.parametrize("mode", [mm.MM_FMM_FP32, mm.MM_PLAIN_FP64])
 def test_second_pass_queue_sizes_leave_the_map_unchanged(mode):
     """Larger triangles go through the device queue to the second mapping
-    pass; with no queue the first pass deals them all, and with a queue too
-    small for the map the batches that do not fit are dealt in place and
-    their reserved slots hold empty jobs.  The fixed-point map is the same
-    in all three cases."""
+    pass; with no queue the first pass deals them all; in FMM mode a queue
+    smaller than about one slot per 12 cells splits the first pass into
+    segments, each drained by the second pass; batches that still do not fit
+    are dealt in place and their reserved slots hold empty jobs.  The
+    fixed-point map is the same in every case."""
     m, pos = small_field(23, 0.45, 0.3, 0.4, hl=1.5, npix=64, rpp=10.0, mass_fn=synthetic.EQUAL)
     maps, stats = [], []
-    for slots in (0, -1, 700):
+    for slots in (0, -1, 700, 64):
         h = mm.create(0.45, 0.3, 0.4, m, pos, 1.5, 64, 10.0, fmm_order=20, flux_fraction_f=0.01,
                       mode=mode, big_queue_slots=slots)
         mm.run(h, 0)
@@ -251,5 +252,44 @@ def test_second_pass_queue_sizes_leave_the_map_unchanged(mode):
         stats.append(mm.get_stats(h))
         mm.destroy(h)
     big = stats[0]["triangles_box"] + stats[0]["triangles_rows"]
-    assert big > 1400, big  # the 700-slot queue overflows
-    assert np.array_equal(maps[0], maps[1]) and np.array_equal(maps[0], maps[2])
+    assert big > 1400, big  # more than a 700-slot queue holds at once
+    for k in (1, 2, 3):
+        assert np.array_equal(maps[0], maps[k]), k
+    if mode == mm.MM_FMM_FP32:  # segments: more launches than one pass pair
+        assert stats[2]["kernel_launches"] > stats[0]["kernel_launches"] + 2
+        assert stats[3]["kernel_launches"] > stats[2]["kernel_launches"]
+
+
+def test_near_critical_count_matches_the_oracle_geometry(oracle_mod):
+    """mm_stats.triangles_near_critical against the same count taken from the
+    oracle's FP64 vertices: triangles not wholly beyond one map edge whose
+    local |mu| (image area / source area) exceeds the threshold."""
+    kappa, gamma, s, hl, npix, rpp = 0.45, 0.3, 0.4, 1.5, 64, 10.0
+    m, pos = small_field(7, kappa, gamma, s, hl, npix, rpp)
+    p = oracle_inputs(oracle_mod, kappa, gamma, s, m, hl, npix, rpp, flux_fraction_f=0.01)
+    n0, n1 = p.n[0], p.n[1]
+    jj, ii = np.meshgrid(np.arange(n1), np.arange(n0), indexing="ij")
+    z = oracle_mod.grid_vertices(p, ii.ravel(), jj.ravel())
+    w = oracle_mod.deflect(p, m, pos, z).reshape(n1, n0, 2)
+    lo = np.array([p.center_y[0] - p.half_length, p.center_y[1] - p.half_length])
+    u = (w - lo) / p.delta                       # source positions in pixel units
+    v00, v10, v01, v11 = u[:-1, :-1], u[:-1, 1:], u[1:, :-1], u[1:, 1:]
+    img2 = p.h[0] * p.h[1] / p.delta ** 2        # twice an image triangle's area
+    for mu_c in (3.0, 30.0, 300.0):
+        ref = 0
+        for a, b, c in ((v00, v10, v11), (v00, v11, v01)):
+            area2 = ((b[..., 0] - a[..., 0]) * (c[..., 1] - a[..., 1]) -
+                     (c[..., 0] - a[..., 0]) * (b[..., 1] - a[..., 1]))
+            px = np.floor(np.stack([a[..., 0], b[..., 0], c[..., 0]]))
+            py = np.floor(np.stack([a[..., 1], b[..., 1], c[..., 1]]))
+            beyond = ((px.max(0) < 0) | (px.min(0) >= npix) | (py.max(0) < 0) |
+                      (py.min(0) >= npix))
+            ref += int(((np.abs(area2) < img2 / mu_c) & (area2 != 0) & ~beyond).sum())
+        _, st = gpu_map(kappa, gamma, s, m, pos, hl, npix, fmm_order=25, critical_mu=mu_c,
+                        **explicit_grid(p))
+        got = st["triangles_near_critical"]
+        assert ref > 0
+        assert abs(got - ref) <= 0.002 * ref + 5, (mu_c, got, ref)
+    _, st = gpu_map(kappa, gamma, s, m, pos, hl, npix, fmm_order=25, critical_mu=1e30,
+                    **explicit_grid(p))
+    assert st["triangles_near_critical"] == 0
