@@ -14,7 +14,9 @@ The C library (``oracle.c``) computes, in FP64 and in the paper's notation:
   smooth sheet of Sec. 3.1, by direct summation over every star;
 * ``magnification_map`` -- inverse polygon mapping (Sec. 3.2): two triangles
   per cell, each pixel receiving area(T n pixel)/|area(T)| from per-pixel
-  Sutherland-Hodgman clipping and the shoelace formula.
+  Sutherland-Hodgman clipping and the shoelace formula;
+* ``irs_map`` -- inverse ray shooting (Sec. 3.2, Table 1's IRS column): each
+  grid vertex is a ray counted in the pixel it lands in.
 """
 import ctypes
 import os
@@ -81,6 +83,11 @@ def lib():
         L.or_map_from_vertices.argtypes = [ctypes.POINTER(Params), _dp, ctypes.c_int64,
                                            ctypes.c_int64, _dp, _dp,
                                            ctypes.POINTER(MapStats), ctypes.c_int]
+        L.or_irs_tile.restype = ctypes.c_int
+        L.or_irs_tile.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _dp, _dp,
+                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.POINTER(ctypes.c_int64), _dp,
+                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
         L.or_tri_rect_area.restype = ctypes.c_double
         L.or_tri_rect_area.argtypes = [_dp, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double]
@@ -190,6 +197,27 @@ def map_from_vertices(params: Params, w_xy, row_begin, row_end, nthreads=None):
     if rc != 0:
         raise ValueError("oracle: bad row range")
     return mu, acc, {"triangles": st.triangles, "dropped": st.dropped, "pieces": st.pieces}
+
+
+def irs_map(params: Params, masses, pos_xy, row_begin=0, row_end=-1, col_begin=0,
+            col_end=-1, nthreads=None):
+    """Inverse ray shooting over the vertices of rows [row_begin, row_end] and
+    columns [col_begin, col_end] (inclusive; -1: the last).  Returns
+    (mu, counts (npix, npix) int64, dropped)."""
+    m = _f64(masses)
+    xy = _f64(pos_xy).reshape(-1, 2)
+    n = params.npix
+    mu = np.zeros((n, n), dtype=np.float64)
+    cnt = np.zeros((n, n), dtype=np.int64)
+    dropped = ctypes.c_int64(0)
+    rc = lib().or_irs_tile(ctypes.byref(params), m.size, _ptr(m), _ptr(xy), int(row_begin),
+                           int(row_end), int(col_begin), int(col_end),
+                           cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                           mu.ctypes.data_as(_dp), ctypes.byref(dropped),
+                           nthreads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle: bad vertex range or out of memory")
+    return mu, cnt, dropped.value
 
 
 def tri_rect_area(tri, xlo, ylo, xhi, yhi):

@@ -19,7 +19,11 @@
  *     triangles, mapped to the source plane, and each pixel receives
  *     area(T intersect pixel) / |area(T)|; the intersection is found by
  *     clipping T against the four half-planes of that single pixel
- *     (Sutherland-Hodgman) and measured with the shoelace formula.
+ *     (Sutherland-Hodgman) and measured with the shoelace formula;
+ *   - inverse ray shooting (Sec. 3.2 and Table 1's IRS column): every grid
+ *     vertex is one ray, counted in the pixel its source position falls in;
+ *     the magnification is the count times the image-plane area per ray over
+ *     the pixel area.
  *
  * Parity pins: see tests/test_oracle_pins.py.  No function here is
  * "parity unpinned".
@@ -98,6 +102,18 @@ int or_map_from_vertices(const or_params *p, const double *w_xy,
                          int64_t row_begin, int64_t row_end,
                          double *mu_out, double *acc_out, or_map_stats *stats,
                          int nthreads);
+
+/* Inverse ray shooting over the vertices of rows [row_begin, row_end] and
+ * columns [col_begin, col_end] (both inclusive; row_end < 0 or col_end < 0
+ * means up to the grid's last vertex): counts (npix*npix, may be NULL) gets
+ * the rays per pixel, mu_out (may be NULL) count * h_x h_y / delta^2, and
+ * *dropped the rays with a non-finite source position.  Pixel (px, py)
+ * holds the rays with floor((w - (center - half_length)) / delta) = (px, py).
+ * Returns 0 on success. */
+int or_irs_tile(const or_params *p, int64_t n_stars, const double *masses,
+                const double *pos_xy, int64_t row_begin, int64_t row_end,
+                int64_t col_begin, int64_t col_end, int64_t *counts, double *mu_out,
+                int64_t *dropped, int nthreads);
 
 /* Area of the intersection of a triangle (x0,y0,x1,y1,x2,y2) with the
  * axis-aligned rectangle [xlo,xhi] x [ylo,yhi]; always >= 0. */

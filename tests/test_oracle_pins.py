@@ -346,3 +346,60 @@ def test_map_rows_partition(oracle_mod):
     a, _ = oracle_mod.magnification_map(p, m, pos, 0, mid)
     b, _ = oracle_mod.magnification_map(p, m, pos, mid, p.n[1] - 1)
     np.testing.assert_allclose(a + b, full, rtol=1e-12, atol=1e-12)
+
+
+def test_irs_zero_star_counts_closed_form(oracle_mod):
+    """Inverse ray shooting with no stars (s = 1): w = (a1 x, a2 y) with
+    a1,2 = 1 - kappa -+ gamma (Sec. 2.1-2.2), so the rays per pixel are the
+    product of per-axis lattice counts.  Every number here is dyadic, so the
+    oracle's FP64 is exact and the counts are compared with exact rational
+    arithmetic (ties on a pixel edge included)."""
+    from fractions import Fraction as Fr
+    kappa, gamma, hl, npix = 0.25, 0.125, 2.0, 16
+    nx, ny, ihx, ihy = 41, 57, 2.5, 3.5
+    p = oracle_mod.derive_params(kappa, gamma, 1.0, [], hl, npix, img_half=(ihx, ihy),
+                                 ray_grid=(nx, ny))
+    mu, cnt, dropped = oracle_mod.irs_map(p, [], np.zeros((0, 2)))
+    assert dropped == 0
+    delta = Fr(2 * hl) / npix
+
+    def axis_counts(a, half, n):
+        c = np.zeros(npix, dtype=np.int64)
+        h = Fr(2 * half) / (n - 1)
+        for i in range(n):
+            k = math.floor((Fr(a) * (-Fr(half) + i * h) + Fr(hl)) / delta)
+            if 0 <= k < npix:
+                c[k] += 1
+        return c
+
+    cx = axis_counts(1 - kappa + gamma, ihx, nx)
+    cy = axis_counts(1 - kappa - gamma, ihy, ny)
+    np.testing.assert_array_equal(cnt, np.outer(cy, cx))   # row = y pixel
+    np.testing.assert_allclose(mu, cnt * p.h[0] * p.h[1] / p.delta ** 2, rtol=1e-15)
+
+
+def test_irs_statistics_agree_with_ipm(oracle_mod):
+    """The paper's consistency check of the two mapping methods (Sec. 3.2,
+    Table 1): on the same field, inverse ray shooting (rays counted per pixel)
+    and inverse polygon mapping (exact areas) give the same magnification
+    averaged over blocks of pixels, within the counting noise of the rays."""
+    kappa, gamma, s, hl, npix, rpp = 0.45, 0.3, 0.4, 1.5, 32, 12.0
+    p0 = oracle_mod.derive_params(kappa, gamma, s, np.ones(4), hl, npix, rays_per_pixel=rpp,
+                                  flux_fraction_f=0.01)
+    R = 1.1 * math.hypot(p0.img_half[0], p0.img_half[1])
+    n = synthetic.n_stars_for((1 - s) * kappa, R, synthetic.EQUAL)
+    m, pos = synthetic.star_field(41, n, R)
+    p = oracle_mod.derive_params(kappa, gamma, s, m, hl, npix, rays_per_pixel=rpp,
+                                 flux_fraction_f=0.01)
+    mu_ipm, _ = oracle_mod.magnification_map(p, m, pos)
+    mu_irs, cnt, dropped = oracle_mod.irs_map(p, m, pos)
+    assert dropped == 0
+    b = 8
+    blk = lambda a: a.reshape(npix // b, b, npix // b, b).sum(axis=(1, 3))
+    rays = blk(cnt.astype(np.float64))
+    ipm_rays = blk(mu_ipm) * p.delta ** 2 / (p.h[0] * p.h[1])   # expected rays per block
+    assert rays.min() > 1000
+    z = (rays - ipm_rays) / np.sqrt(ipm_rays)
+    assert np.abs(z).max() < 5.0, z
+    # the totals agree to the lattice's edge effects: much better than Poisson
+    assert abs(rays.sum() / ipm_rays.sum() - 1) < 3.0 / math.sqrt(ipm_rays.sum())
