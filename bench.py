@@ -67,10 +67,16 @@ def parse_args():
                     help="override the workload's rays per pixel (smaller profiling cases)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the map steps only: no FP64 band, end-to-end or CPU legs")
+    ap.add_argument("--irs", action="store_true",
+                    help="inverse ray shooting (rays counted per pixel) instead of polygon "
+                         "mapping, for the map steps; implies --kernel-only")
     ap.add_argument("--autotune", action="store_true",
                     help="let mm_create choose leaf size, sub-cell levels and work-item rows "
                          "by timing (mm_options.autotune; no cache file)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.irs:
+        a.kernel_only = True
+    return a
 
 
 def dist_env():
@@ -211,7 +217,8 @@ def run_native(args):
     m, pos = wl.stars()
     args_map = (wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, wl.npix, wl.rays_per_pixel)
     stream = torch.cuda.Stream(device=dev)
-    h = mm.create(*args_map, fmm_order=wl.fmm_order, time_stages=True, autotune=args.autotune)
+    h = mm.create(*args_map, fmm_order=wl.fmm_order, time_stages=True, autotune=args.autotune,
+                  mode=mm.MM_FMM_IRS if args.irs else mm.MM_FMM_FP32)
     st0 = mm.get_stats(h)
     # the end-to-end leg creates its handles with the settings chosen here
     tuned = (dict(leaf_size=st0["leaf_size"], sub_levels=st0["sub_levels"],
@@ -349,7 +356,8 @@ def run_native(args):
                    "ray_grid": st["params"]["n"], "rays": rays, "fmm_order": p,
                    "eval_order": pe, "sub_levels": st["sub_levels"],
                    "leaf_size": st["leaf_size"], "rows_per_item": st["rows_per_item"],
-                   "autotuned": st["autotuned"], "l2": "flushed before every step (256 MiB write)",
+                   "autotuned": st["autotuned"], "mapping": "irs" if args.irs else "ipm",
+                   "l2": "flushed before every step (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "maps_per_s": world / (ms_per_step * 1e-3),
         "stages_ms": {k: st[k] for k in ("ms_tree", "ms_expansions", "ms_shoot", "ms_first_pass",

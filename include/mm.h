@@ -54,7 +54,13 @@ typedef enum {
 
 typedef enum {
   MM_FMM_FP32 = 0,  /* FMM deflection, FP32 per ray, FP64 expansions (default) */
-  MM_PLAIN_FP64 = 1 /* direct sum over every star in FP64 (no tree) */
+  MM_PLAIN_FP64 = 1, /* direct sum over every star in FP64 (no tree) */
+  MM_FMM_IRS = 2     /* inverse ray shooting (Sec. 3.2, Table 1's IRS column):
+                        the deflection of MM_FMM_FP32, then every grid vertex
+                        (ray) adds one count to the pixel it lands in; mu =
+                        count h_x h_y / delta^2, and mm_get_map_fixed returns
+                        the counts.  triangles_dropped counts rays with a
+                        non-finite position; no batching, no autotuning. */
 } mm_mode;
 
 /* Options; a zero-initialised struct (or NULL) selects the defaults. */

@@ -22,7 +22,7 @@ import numpy as np
 from . import build as _build
 
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ETIMEOUT, MM_ESTATE = range(6)
-MM_FMM_FP32, MM_PLAIN_FP64 = 0, 1
+MM_FMM_FP32, MM_PLAIN_FP64, MM_FMM_IRS = 0, 1, 2
 _STATUS = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ECUDA", 4: "MM_ETIMEOUT",
            5: "MM_ESTATE"}
 

@@ -691,7 +691,11 @@ static mm_status clear_map(mm_map *h, cudaStream_t st) {
   return MM_OK;
 }
 
-static double map_scale(const mm_params &P) {
+// mu per accumulator unit: a triangle's 2^32 units stand for its image
+// area h_x h_y / 2 (IPM); a ray's one count for its cell's h_x h_y (IRS)
+static double map_scale(const mm_map *h) {
+  const mm_params &P = h->P;
+  if (h->mode == MM_FMM_IRS) return P.h[0] * P.h[1] / (P.delta * P.delta);
   return std::ldexp(0.5 * P.h[0] * P.h[1] / (P.delta * P.delta), -32);
 }
 
@@ -716,7 +720,7 @@ static mm_status alloc_map_buffers(mm_map *h) {
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
     const bool fits_l2 = 16.0 * (double)h->P.npix * (double)h->P.npix <= 0.5 * (double)l2;
-    const int32_t want = h->opt.big_queue_slots;
+    const int32_t want = h->mode == MM_FMM_IRS ? -1 : h->opt.big_queue_slots;
     h->bigq_cap = want < 0 ? 0
                   : want > 0 ? (int64_t)want
                   : fits_l2  ? std::min<int64_t>(int64_t(1) << 27,
@@ -793,6 +797,19 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     CKS(record(h, 2, st));
     const int64_t work =
         (int64_t)h->md.strips * ((h->md.row_blocks + h->md.item_stride - 1) / h->md.item_stride);
+    if (h->mode == MM_FMM_IRS) {
+      LCH(launch_shoot_irs(h->md, work, h->md.square_cells != 0, h->counter.p, h->err.p,
+                          shoot_grid(), st));
+      h->last_segments = 0;
+      CKS(record(h, 5, st));
+      CKS(record(h, 3, st));
+      LCH(launch_normalize(h->acc.p, h->span.p, P.npix, map_scale(h), h->map.p, st));
+      CKS(record(h, 4, st));
+      h->ev_recorded = h->opt.time_stages != 0;
+      h->last_stream = st;
+      h->ran = true;
+      return MM_OK;
+    }
     const int64_t nseg = std::max<int64_t>(1, std::min(h->segments, work));
     const int64_t per = (work + nseg - 1) / nseg;
     int64_t k = 0;
@@ -813,7 +830,7 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     CKS(record(h, 5, st));
   }
   CKS(record(h, 3, st));
-  LCH(launch_normalize(h->acc.p, h->span.p, P.npix, map_scale(P), h->map.p, st));
+  LCH(launch_normalize(h->acc.p, h->span.p, P.npix, map_scale(h), h->map.p, st));
   CKS(record(h, 4, st));
   h->ev_recorded = h->opt.time_stages != 0;
   h->last_stream = st;
@@ -851,7 +868,7 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
     return fail(MM_EINVAL, "fmm_order %d outside [0, %d]", fmm_order, MM_PMAX);
   if (leaf_size < 0 || leaf_size > 1024)
     return fail(MM_EINVAL, "leaf_size %d outside [0, 1024]", leaf_size);
-  if (h->opt.mode != MM_FMM_FP32 && h->opt.mode != MM_PLAIN_FP64)
+  if (h->opt.mode != MM_FMM_FP32 && h->opt.mode != MM_PLAIN_FP64 && h->opt.mode != MM_FMM_IRS)
     return fail(MM_EINVAL, "unknown mode %d", h->opt.mode);
   if (!(h->opt.critical_mu >= 0.0) || !std::isfinite(h->opt.critical_mu))
     return fail(MM_EINVAL, "critical_mu %g is negative or not finite", h->opt.critical_mu);
@@ -1245,7 +1262,7 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
     CKS(record(h, 5, st));
     LCH(launch_big_ipm(h->md, st));
     CKS(record(h, 3, st));
-    LCH(launch_normalize(h->acc.p, h->span.p, h->P.npix, map_scale(h->P), h->map.p, st));
+    LCH(launch_normalize(h->acc.p, h->span.p, h->P.npix, map_scale(h), h->map.p, st));
     CKS(record(h, 4, st));
     h->ev_recorded = h->opt.time_stages != 0;
     h->last_stream = st;
@@ -1351,9 +1368,9 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
   memset(out, 0, sizeof *out);
   out->params = h->P;
   out->mode = h->mode;
-  out->fmm_order = h->mode == MM_FMM_FP32 ? h->p : 0;
-  out->eval_order = h->mode == MM_FMM_FP32 ? h->p_eval : 0;
-  out->sub_levels = h->mode == MM_FMM_FP32 ? h->sub : 0;
+  out->fmm_order = h->mode != MM_PLAIN_FP64 ? h->p : 0;
+  out->eval_order = h->mode != MM_PLAIN_FP64 ? h->p_eval : 0;
+  out->sub_levels = h->mode != MM_PLAIN_FP64 ? h->sub : 0;
   out->leaf_size = h->leaf_size;
   out->depth = h->depth;
   out->n_stars = h->N;
@@ -1366,7 +1383,7 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
   out->ms_tree = out->ms_expansions = out->ms_shoot = out->ms_normalize = out->ms_total = -1.0;
   out->ms_first_pass = out->ms_second_pass = -1.0;
   if (h->last_stream || h->ran) CK(cudaStreamSynchronize(h->last_stream));
-  if (h->mode == MM_FMM_FP32 && h->n_nodes > 0) {
+  if (h->mode != MM_PLAIN_FP64 && h->n_nodes > 0) {
     std::vector<int32_t> fc(h->n_nodes);
     CK(cudaMemcpy(fc.data(), h->first_child.p, h->n_nodes * sizeof(int32_t),
                   cudaMemcpyDeviceToHost));
@@ -1407,7 +1424,7 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
     float a = 0, b = 0, c = 0, d = 0;
     CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[4]));
     out->ms_total = a;
-    if (h->mode == MM_FMM_FP32) {
+    if (h->mode != MM_PLAIN_FP64) {
       CK(cudaEventElapsedTime(&b, h->ev[0], h->ev[1]));
       CK(cudaEventElapsedTime(&c, h->ev[1], h->ev[2]));
       out->ms_tree = b;

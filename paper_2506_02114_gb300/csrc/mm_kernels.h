@@ -86,6 +86,10 @@ void build_operator_tables(int p, std::vector<double2> &MM, std::vector<double2>
 
 // ---- shooting + mapping (shoot.cu) -----------------------------------------
 // The second pass over the map's queued larger triangles (no-op without a queue).
+// inverse ray shooting of one map's work items (no second pass)
+cudaError_t launch_shoot_irs(const MapDev &m, int64_t total_work, bool square,
+                             unsigned long long *counter, unsigned *err, int grid,
+                             cudaStream_t st);
 cudaError_t launch_big_ipm(const MapDev &m, cudaStream_t st);
 // h_single: the map by value when n_maps == 1 (else NULL: maps from d_maps)
 cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n_maps,

@@ -383,6 +383,60 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
   if (last_map >= 0) flush_counters(BATCH ? maps[last_map] : M1, cnt, lane);
 }
 
+// Inverse ray shooting (Sec. 3.2; the IRS column of Table 1): every grid
+// vertex is one ray, and the pixel it lands in gains one count.  The work
+// items, deflection and culling are k_shoot_ipm's; lane l < 31 owns vertex
+// column 31 s + l (lane 31 only the grid's last column) and a work item owns
+// its vertex rows [jb, je) (the map's last item also je), so every ray is
+// counted once.  Rows proven to land beyond a map edge are skipped: none of
+// their rays can count, and a culled vertex is never non-finite (a ray on a
+// star lies inside that star's culling radius).
+template <bool SQUARE>
+__global__ void __launch_bounds__(256, MM_SHOOT_MINB)
+    k_shoot_irs(const MapDev M, int64_t total_work, unsigned long long *work_counter,
+                unsigned *err) {
+  const int lane = threadIdx.x & 31;
+  IpmCounters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+  while (true) {
+    unsigned long long w = 0;
+    if (lane == 0) w = atomicAdd(work_counter, 1ull);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if ((int64_t)w >= total_work) break;
+    const int64_t local = (int64_t)w - M.work_begin;
+    const int64_t s = local % M.strips, b = (local / M.strips) * M.item_stride;
+    const int64_t i = M.col_begin + s * MM_STRIP + lane;
+    const int64_t jb = M.row_begin + b * M.rows_per_item;
+    const int64_t je = min(jb + (int64_t)M.rows_per_item, M.row_end);
+    const int64_t jl = je == M.row_end ? je : je - 1;  // last vertex row owned
+    const bool vvalid = i <= M.col_end;
+    const bool owner = vvalid && (lane < MM_STRIP || i == M.col_end);
+    const int cx = __ldg(&M.col_cell[vvalid ? i : M.col_end]);
+    RunAcc ra = {-1, 0ull};
+    for (int64_t j = jb; j <= jl; j++) {
+      const int leaf = lookup_leaf(M, cx, __ldg(&M.row_cell[j]));
+      if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
+      if (M.cull) {
+        int run;
+        if (row_cull_side<SQUARE>(M, leaf, i, j, vvalid, run) != MM_CULL_NONE) {
+          const int64_t skip = min((int64_t)run, jl - j + 1);
+          if (lane == 0) cnt.culled += (unsigned)skip;
+          j += skip - 1;
+          continue;
+        }
+      }
+      const Vtx v = shoot_point<SQUARE, false>(M, leaf, i, j, 0.f, 0.f, vvalid);
+      if (owner) {
+        if (v.px == MM_VTX_INVALID)
+          cnt.dropped++;
+        else if (v.px >= 0 && v.px < M.npix && v.py >= 0 && v.py < M.npix)
+          run_add(M, ra, (long long)v.py * M.npix + v.px, 1ull);
+      }
+    }
+    run_flush(M, ra);
+  }
+  flush_counters(M, cnt, lane);
+}
+
 // Second pass over the larger triangles k_shoot_ipm (or k_ipm_vertices)
 // queued for the map: each warp takes batches of 32 from the device queue
 // and deals out their pixel rows and partially covered pixels
@@ -516,6 +570,17 @@ cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n
                                              st)
                 : launch_shoot_t<false, true>(d_maps, none, n_maps, total_work, counter, err,
                                               grid, st);
+}
+
+cudaError_t launch_shoot_irs(const MapDev &m, int64_t total_work, bool square,
+                             unsigned long long *counter, unsigned *err, int grid,
+                             cudaStream_t st) {
+  if (total_work <= 0) return cudaSuccess;
+  if (square)
+    k_shoot_irs<true><<<grid, 256, 0, st>>>(m, total_work, counter, err);
+  else
+    k_shoot_irs<false><<<grid, 256, 0, st>>>(m, total_work, counter, err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_big_ipm(const MapDev &m, cudaStream_t st) {

@@ -293,3 +293,67 @@ def test_near_critical_count_matches_the_oracle_geometry(oracle_mod):
     _, st = gpu_map(kappa, gamma, s, m, pos, hl, npix, fmm_order=25, critical_mu=1e30,
                     **explicit_grid(p))
     assert st["triangles_near_critical"] == 0
+
+
+def test_irs_counts_match_the_oracle(oracle_mod):
+    """Inverse ray shooting (MM_FMM_IRS) against the oracle's FP64 rays: a
+    ray's pixel is a floating-point decision, so the counts agree exactly
+    except for rays within 2.5 x the deflection tolerance of a pixel edge;
+    each such ray may land on either side.  Checked per pixel: 0 <= gpu - (oracle without them) <= the
+    pixels they can reach.  Also: the full-map mean within counting noise of
+    the polygon-mapping map, and the same counts with culling off."""
+    kappa, gamma, s, hl, npix, rpp = 0.45, 0.3, 0.4, 1.5, 64, 10.0
+    m, pos = small_field(7, kappa, gamma, s, hl, npix, rpp)
+    p = oracle_inputs(oracle_mod, kappa, gamma, s, m, hl, npix, rpp, flux_fraction_f=0.01)
+    n0, n1 = p.n[0], p.n[1]
+    jj, ii = np.meshgrid(np.arange(n1), np.arange(n0), indexing="ij")
+    z = oracle_mod.grid_vertices(p, ii.ravel(), jj.ravel())
+    w = oracle_mod.deflect(p, m, pos, z)
+    lo = np.array([p.center_y[0] - p.half_length, p.center_y[1] - p.half_length])
+    u = (w - lo) / p.delta
+    f = np.floor(u).astype(np.int64)
+    # per ray: 2.5 x the deflection tolerance, in pixels (>= 1e-4 px)
+    zz = z.reshape(-1, 2)
+    alpha = np.stack([(1 - kappa + gamma) * zz[:, 0], (1 - kappa - gamma) * zz[:, 1]], 1) - w
+    scale = np.maximum(np.hypot(alpha[:, 0], alpha[:, 1]), math.sqrt(p.kappa_star))
+    eps = np.maximum(1e-4, 2.5 * DEFLECTION_TOL * scale / p.delta)[:, None]
+    d = u - f
+    near_lo, near_hi = d < eps, d > 1 - eps
+    edge = (near_lo | near_hi).any(axis=1)
+    inside = lambda q: (q[:, 0] >= 0) & (q[:, 0] < npix) & (q[:, 1] >= 0) & (q[:, 1] < npix)
+    sure = ~edge & inside(f)
+    ref = np.zeros((npix, npix), dtype=np.int64)
+    np.add.at(ref, (f[sure, 1], f[sure, 0]), 1)
+    allow = np.zeros((npix, npix), dtype=np.int64)
+    fe, le, he = f[edge], near_lo[edge], near_hi[edge]
+    for ox in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            okx = (ox == 0) | ((ox == -1) & le[:, 0]) | ((ox == 1) & he[:, 0])
+            oky = (oy == 0) | ((oy == -1) & le[:, 1]) | ((oy == 1) & he[:, 1])
+            q = fe + np.array([ox, oy])
+            sel = okx & oky & inside(q)
+            np.add.at(allow, (q[sel, 1], q[sel, 0]), 1)
+    h = mm.create(kappa, gamma, s, m, pos, hl, npix, fmm_order=25, mode=mm.MM_FMM_IRS,
+                  **explicit_grid(p))
+    mm.run(h, 0)
+    cnt = mm.get_map_fixed(h).astype(np.int64)
+    mu = mm.get_map(h)
+    st = mm.get_stats(h)
+    mm.destroy(h)
+    assert edge.sum() < 0.01 * edge.size and st["triangles_dropped"] == 0
+    diff = cnt - ref
+    assert diff.min() >= 0 and (diff <= allow).all(), (diff.min(), (diff - allow).max())
+    assert diff.sum() <= edge.sum()
+    np.testing.assert_allclose(mu, cnt * p.h[0] * p.h[1] / p.delta ** 2, rtol=1e-6)
+    # the oracle's own IRS map agrees the same way
+    _, cnt_or, _ = oracle_mod.irs_map(p, m, pos)
+    assert np.abs(cnt_or - cnt).sum() <= 2 * edge.sum()
+    # the IPM map's mean, within the rays' counting noise
+    mu_ipm, _ = oracle_mod.magnification_map(p, m, pos)
+    assert abs(mu.mean() / mu_ipm.mean() - 1) < 3.0 / math.sqrt(cnt.sum())
+    # culling skips only rays proven to land beyond the map: same counts
+    h = mm.create(kappa, gamma, s, m, pos, hl, npix, fmm_order=25, mode=mm.MM_FMM_IRS,
+                  cull=False, **explicit_grid(p))
+    mm.run(h, 0)
+    assert np.array_equal(mm.get_map_fixed(h).astype(np.int64), cnt)
+    mm.destroy(h)
