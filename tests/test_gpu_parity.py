@@ -357,3 +357,58 @@ def test_irs_counts_match_the_oracle(oracle_mod):
     mm.run(h, 0)
     assert np.array_equal(mm.get_map_fixed(h).astype(np.int64), cnt)
     mm.destroy(h)
+
+
+def test_extreme_magnification_map(oracle_mod):
+    """Sec. 5's extreme case, scaled down: kappa = 0.66717, gamma = 0.33383
+    (mu_macro = -1500), s = 1 - 5e-5, Salpeter stars; 128^2 pixels over a
+    4 x 4 source region with ~100 rays landing per pixel (a 54 x 34 747 ray
+    grid 1000 times longer in y than in x).  The paper saw large FP32 errors
+    here; the FP32 per-ray path (FP64 sub-cell centre images, macro factor
+    formed in FP64) must meet the map tolerances, with sampled source
+    positions within 1e-3 pixel of the oracle's."""
+    kappa, gamma, s, hl, npix = 0.66717, 0.33383, 1 - 5e-5, 2.0, 128
+    mu_macro = 1.0 / ((1 - kappa) ** 2 - gamma ** 2)
+    rpp = 100.0 / abs(mu_macro)
+    p0 = oracle_inputs(oracle_mod, kappa, gamma, s, np.ones(4), hl, npix, rpp)
+    R = 1.05 * math.hypot(p0.img_half[0], p0.img_half[1])
+    n = synthetic.n_stars_for((1 - s) * kappa, R, synthetic.SALPETER_01_1)
+    m, pos = synthetic.star_field(77, n, R, synthetic.SALPETER_01_1)
+    p = oracle_inputs(oracle_mod, kappa, gamma, s, m, hl, npix, rpp)
+    assert abs(p.mu_macro + 1500.0) < 0.1 and p.n[1] > 600 * p.n[0]
+    mu_ref, st_ref = oracle_mod.magnification_map(p, m, pos)
+    h = mm.create(kappa, gamma, s, m, pos, hl, npix, fmm_order=25, **explicit_grid(p))
+    mm.run(h, 0)
+    mu = mm.get_map(h)
+    rng = np.random.default_rng(4)
+    zs = oracle_mod.grid_vertices(p, rng.integers(0, p.n[0], 4000), rng.integers(0, p.n[1], 4000))
+    w = mm.shoot_points(h, zs)
+    mm.destroy(h)
+    # kappa_star = 3.3e-5: the relative measure's floor sqrt(kappa_star) is
+    # 0.006 theta_E, a fifth of a pixel, below what FP32 offsets of ~100 px
+    # from a sub-cell's FP64 centre image resolve; the error that decides the
+    # map is the one in pixels
+    err_px = np.hypot(*(w - oracle_mod.deflect(p, m, pos, zs)).T) / p.delta
+    assert err_px.max() <= 1e-3, err_px.max()
+    assert_map_parity(mu, mu_ref, p.mu_macro)
+
+
+def test_map_centre_offset(oracle_mod):
+    """A map centred off the origin (Sec. 2.3: the shooting region is the
+    macro pre-image of the offset map plus the border) against the oracle."""
+    kappa, gamma, s, hl, npix, rpp = 0.45, 0.3, 0.4, 1.0, 48, 10.0
+    cy = (0.7, -0.4)
+    p0 = oracle_inputs(oracle_mod, kappa, gamma, s, np.ones(4), hl, npix, rpp,
+                       flux_fraction_f=0.01, center_y=cy)
+    R = 1.1 * (math.hypot(p0.img_center[0], p0.img_center[1]) +
+               math.hypot(p0.img_half[0], p0.img_half[1]))
+    n = synthetic.n_stars_for((1 - s) * kappa, R, synthetic.EQUAL)
+    m, pos = synthetic.star_field(13, n, R)
+    p = oracle_inputs(oracle_mod, kappa, gamma, s, m, hl, npix, rpp, flux_fraction_f=0.01,
+                      center_y=cy)
+    assert abs(p.img_center[0]) > 0.5 and abs(p.img_center[1]) > 0.5
+    mu_ref, _ = oracle_mod.magnification_map(p, m, pos)
+    mu, st = gpu_map(kappa, gamma, s, m, pos, hl, npix, rays_per_pixel=rpp, fmm_order=25,
+                     flux_fraction_f=0.01, center_y=cy)
+    assert st["params"]["n"] == list(p.n)
+    assert_map_parity(mu, mu_ref, p.mu_macro)
