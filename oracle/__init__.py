@@ -40,6 +40,7 @@ class Params(ctypes.Structure):
         ("center_y", ctypes.c_double * 2), ("img_center", ctypes.c_double * 2),
         ("img_half", ctypes.c_double * 2), ("n", ctypes.c_int64 * 2),
         ("h", ctypes.c_double * 2), ("x0", ctypes.c_double * 2),
+        ("star_rect", ctypes.c_double * 2),
     ]
 
     def as_dict(self):
@@ -68,6 +69,9 @@ def lib():
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64, _dp,
             ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _dp,
             _dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(Params)]
+        L.or_alpha_rect.restype = None
+        L.or_alpha_rect.argtypes = [ctypes.POINTER(Params), ctypes.c_double, ctypes.c_double,
+                                    _dp, _dp]
         L.or_deflect.restype = None
         L.or_deflect.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _dp, _dp,
                                  ctypes.c_int64, _dp, _dp, ctypes.c_int]
@@ -109,7 +113,7 @@ def default_threads():
 
 def derive_params(kappa, gamma, smooth_fraction, masses, half_length, npix,
                   rays_per_pixel=0.0, flux_fraction_f=0.0, center_y=None,
-                  img_half=None, ray_grid=None) -> Params:
+                  img_half=None, ray_grid=None, star_rect=None) -> Params:
     m = _f64(masses)
     p = Params()
     cy = _f64(center_y) if center_y is not None else None
@@ -124,7 +128,17 @@ def derive_params(kappa, gamma, smooth_fraction, masses, half_length, npix,
         ctypes.byref(p))
     if rc != 0:
         raise ValueError("oracle: invalid parameters")
+    if star_rect is not None:
+        p.star_rect[0], p.star_rect[1] = float(star_rect[0]), float(star_rect[1])
     return p
+
+
+def alpha_rect(params: Params, x, y):
+    """App. B's deflection of the rectangular sheet of params.star_rect at (x, y)."""
+    ax, ay = ctypes.c_double(), ctypes.c_double()
+    lib().or_alpha_rect(ctypes.byref(params), float(x), float(y), ctypes.byref(ax),
+                        ctypes.byref(ay))
+    return complex(ax.value, ay.value)
 
 
 def deflect(params: Params, masses, pos_xy, z_xy, nthreads=None):

@@ -97,6 +97,36 @@ int or_derive_params(double kappa, double gamma, double smooth_fraction,
 /* Lens equation, direct sum (Sec. 2.2; smooth sheet of Sec. 3.1)           */
 /* ------------------------------------------------------------------------ */
 
+/* App. B: for the sheet of convergence -kappa_star on |x| <= c1, |y| <= c2,
+ * with corner c = c1 + i c2,
+ *   alpha_s(z) = (-kappa_star i / pi) [ (c - zb) log(c - zb) - (cb - zb) log(cb - zb)
+ *                 + (-c - zb) log(-c - zb) - (-cb - zb) log(-cb - zb) ]
+ *                - kappa_star (c + cb + z + zb) B_(c1,c2)(z)
+ *                - kappa_star 2 (c + cb) B_(inf,c2)(z) H(Re z - c1),
+ * zb = conj(z), cb = conj(c), principal logarithms; B is the closed box
+ * indicator and H the unit step with H(0) = 1. */
+static double complex rect_sheet_alpha(double kappa_star, double c1, double c2,
+                                       double complex z) {
+  const double pi = 3.14159265358979323846;
+  const double complex c = c1 + I * c2, cb = conj(c), zb = conj(z);
+  const double complex t1 = (c - zb) * clog(c - zb), t2 = (cb - zb) * clog(cb - zb);
+  const double complex t3 = (-c - zb) * clog(-c - zb), t4 = (-cb - zb) * clog(-cb - zb);
+  double complex a = (-kappa_star * I / pi) * (t1 - t2 + t3 - t4);
+  const double x = creal(z), y = cimag(z);
+  const int in_strip = (-c2 <= y && y <= c2);
+  if (in_strip && -c1 <= x && x <= c1) a -= kappa_star * (c + cb + z + zb);
+  if (in_strip && x - c1 >= 0.0) a -= kappa_star * 2.0 * (c + cb);
+  return a;
+}
+
+void or_alpha_rect(const or_params *p, double x, double y, double *ax, double *ay) {
+  double complex a = 0;
+  if (p->star_rect[0] > 0 && p->star_rect[1] > 0)
+    a = rect_sheet_alpha(p->kappa_star, p->star_rect[0], p->star_rect[1], x + I * y);
+  *ax = creal(a);
+  *ay = cimag(a);
+}
+
 static void lens_map_point(const or_params *p, int64_t n_stars,
                            const double *masses, const double *pos_xy,
                            double x, double y, double *wx, double *wy) {
@@ -107,8 +137,11 @@ static void lens_map_point(const or_params *p, int64_t n_stars,
     double complex zi = pos_xy[2 * i] + I * pos_xy[2 * i + 1];
     alpha_star += masses[i] / (conj(z) - conj(zi));
   }
-  /* circular sheet of convergence -kappa_star, inside the star disk */
+  /* sheet of convergence -kappa_star over the star region: inside a star
+   * disk -kappa_star z; over a rectangle the closed form of App. B */
   double complex alpha_s = -p->kappa_star * z;
+  if (p->star_rect[0] > 0 && p->star_rect[1] > 0)
+    alpha_s = rect_sheet_alpha(p->kappa_star, p->star_rect[0], p->star_rect[1], z);
   double complex w = (1.0 - p->kappa) * z + p->gamma * conj(z) - alpha_star - alpha_s;
   *wx = creal(w);
   *wy = cimag(w);

@@ -23,7 +23,10 @@
  *   - inverse ray shooting (Sec. 3.2 and Table 1's IRS column): every grid
  *     vertex is one ray, counted in the pixel its source position falls in;
  *     the magnification is the count times the image-plane area per ray over
- *     the pixel area.
+ *     the pixel area;
+ *   - the smooth sheet of a rectangular star region (App. B): the closed
+ *     form with its four complex logarithms and the boxcar / step terms that
+ *     keep it continuous across the branch cuts, valid inside and outside.
  *
  * Parity pins: see tests/test_oracle_pins.py.  No function here is
  * "parity unpinned".
@@ -57,6 +60,10 @@ typedef struct {
   int64_t n[2];               /* rays (grid vertices) per axis */
   double h[2];                /* ray spacing per axis */
   double x0[2];               /* position of vertex (0,0) */
+  /* star region: star_rect = (c1, c2) > 0 places the smooth sheet of
+   * convergence -kappa_star on the rectangle |x| <= c1, |y| <= c2 (App. B);
+   * zeros (the default) on the disk holding the stars (footnote of Sec. 3.1) */
+  double star_rect[2];
 } or_params;
 
 typedef struct {
@@ -75,6 +82,10 @@ int or_derive_params(double kappa, double gamma, double smooth_fraction,
                      double flux_fraction_f, const double *center_y,
                      const double *img_half_opt, const int64_t *ray_grid_opt,
                      or_params *out);
+
+/* Deflection alpha_s(z) of the rectangular sheet of p->star_rect (App. B),
+ * at one point; zero when p->star_rect is unset. */
+void or_alpha_rect(const or_params *p, double x, double y, double *ax, double *ay);
 
 /* w at n image-plane points z (interleaved x,y) for the given stars. */
 void or_deflect(const or_params *p, int64_t n_stars, const double *masses,

@@ -125,6 +125,26 @@ def star_field(seed: int, n_stars: int, radius: float, mass_fn: MassFunction = E
     return m, pos
 
 
+def star_field_rect(seed: int, n_stars: int, half_widths, mass_fn: MassFunction = EQUAL):
+    """n_stars point masses uniform in the rectangle |x| <= c1, |y| <= c2
+    (half_widths = (c1, c2)).  Returns (masses, positions) like star_field."""
+    c1, c2 = float(half_widths[0]), float(half_widths[1])
+    x = c1 * (2.0 * uniform(seed, 0, n_stars) - 1.0)
+    y = c2 * (2.0 * uniform(seed, 1, n_stars) - 1.0)
+    pos = np.stack([x, y], axis=1)
+    if mass_fn.name == "equal":
+        m = np.ones(n_stars)
+    else:
+        m = mass_fn.sample(uniform(seed, 2, n_stars), uniform(seed, 3, n_stars))
+    return m, pos
+
+
+def n_stars_for_rect(kappa_star: float, half_widths, mass_fn: MassFunction) -> int:
+    """Star count giving surface density kappa_star/pi per unit area in the
+    rectangle of the given half-widths."""
+    return int(round(kappa_star * 4.0 * half_widths[0] * half_widths[1] / (math.pi * mass_fn.mean)))
+
+
 def n_stars_for(kappa_star: float, radius: float, mass_fn: MassFunction) -> int:
     """Star count giving surface density kappa_star/pi per unit area (theta_E
     units) in a disk of the given radius."""

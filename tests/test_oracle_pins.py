@@ -403,3 +403,81 @@ def test_irs_statistics_agree_with_ipm(oracle_mod):
     assert np.abs(z).max() < 5.0, z
     # the totals agree to the lattice's edge effects: much better than Poisson
     assert abs(rays.sum() / ipm_rays.sum() - 1) < 3.0 / math.sqrt(ipm_rays.sum())
+
+
+# ---------------------------------------------------------------------------
+# rectangular star region (App. B)
+# ---------------------------------------------------------------------------
+
+def _rect_params(oracle_mod, c1, c2, kappa=0.4, s=0.5):
+    return oracle_mod.derive_params(kappa, 0.3, s, np.ones(4), 2.0, 16, rays_per_pixel=4.0,
+                                    star_rect=(c1, c2))
+
+
+def test_rect_sheet_matches_its_defining_integral(oracle_mod):
+    """App. B's closed form against the defining area integral of the sheet,
+    summed as a lattice of point masses (midpoint rule, O(h^2)): outside the
+    rectangle and, with the lattice cell holding the point left out (its
+    integral vanishes by symmetry), inside it."""
+    c1, c2 = 5.0, 3.0
+    p = _rect_params(oracle_mod, c1, c2)
+    ks = p.kappa_star
+    nx, ny = 1000, 600
+    hx, hy = 2 * c1 / nx, 2 * c2 / ny
+    X, Y = np.meshgrid(-c1 + (np.arange(nx) + 0.5) * hx, -c2 + (np.arange(ny) + 0.5) * hy)
+    Z = X + 1j * Y
+    mcell = -ks * hx * hy / math.pi           # point mass of one lattice cell
+    for z in (8 + 2j, 1 + 5j, -7 - 4j, 5.5 + 0.2j):
+        ref = np.sum(mcell / np.conj(z - Z))
+        got = oracle_mod.alpha_rect(p, z.real, z.imag)
+        assert abs(got - ref) < 1e-6 * abs(ref), (z, got, ref)
+    for kx, ky in ((500, 300), (123, 77), (990, 20)):
+        z = Z[ky, kx]
+        d = np.conj(z - Z)
+        d[ky, kx] = np.inf
+        ref = np.sum(mcell / d)
+        got = oracle_mod.alpha_rect(p, z.real, z.imag)
+        assert abs(got - ref) < 2e-4 * ks * c1, (z, got, ref)
+
+
+def test_rect_sheet_symmetry_continuity_and_limit(oracle_mod):
+    """Odd in z and mirror-symmetric about the real axis (the sheet is);
+    continuous across the rectangle's edges (the boxcar and step terms undo
+    the branch cuts); and near the centre of a large square it is the
+    disk's -kappa_star z."""
+    c1, c2 = 4.0, 2.5
+    p = _rect_params(oracle_mod, c1, c2)
+    a = lambda z: oracle_mod.alpha_rect(p, z.real, z.imag)
+    assert abs(a(0j)) < 1e-14
+    for z in (1.3 + 0.4j, -3.1 + 2.0j, 6.0 - 3.0j, 0.2 - 2.4j):
+        assert abs(a(-z) + a(z)) < 1e-12
+        assert abs(a(z.conjugate()) - a(z).conjugate()) < 1e-12
+    e = 1e-9
+    for z in (c1 + 0.7j, -c1 - 1.9j, 1.1 + c2 * 1j, -2.2 - c2 * 1j, c1 + 2.4999j):
+        d = z / abs(z)                         # outward-ish step across the edge
+        assert abs(a(z + e * d) - a(z - e * d)) < 1e-7, z
+    big = _rect_params(oracle_mod, 1000.0, 1000.0)
+    for z in (3 + 2j, -5 + 7j):
+        got = oracle_mod.alpha_rect(big, z.real, z.imag)
+        assert abs(got + big.kappa_star * z) < 1e-4 * abs(big.kappa_star * z)
+
+
+def test_rect_sheet_compensates_star_mass(oracle_mod):
+    """As for the disk (Sec. 3.1): stars uniform in the rectangle plus its
+    sheet have zero mean deflection inside it, over realisations."""
+    kappa, gamma, s = 0.6, 0.0, 0.0
+    c1, c2 = 24.0, 12.0
+    z0 = np.array([[9.0, -5.0]])
+    ks = (1 - s) * kappa
+    n = synthetic.n_stars_for_rect(ks, (c1, c2), synthetic.EQUAL)
+    p = oracle_mod.derive_params(kappa, gamma, s, np.ones(n), 2.0, 8, rays_per_pixel=1.0,
+                                 star_rect=(c1, c2))
+    nets = []
+    for seed in range(60):
+        m, pos = synthetic.star_field_rect(900 + seed, n, (c1, c2))
+        w = oracle_mod.deflect(p, m, pos, z0)
+        nets.append(((1 - kappa) * z0 - w)[0])
+    nets = np.array(nets)
+    mean = nets.mean(0)
+    sem = nets.std(0) / math.sqrt(len(nets))
+    assert np.all(np.abs(mean) < 4 * sem + 0.05), (mean, sem)
