@@ -142,6 +142,19 @@ typedef struct {
   double critical_mu;       /* statistics: a mapped triangle whose local |mu|
                                (image area / source area) exceeds this counts
                                as near-critical (mm_stats); 0 -> 1e3 */
+  double star_rect[2];      /* > 0 (both): the stars fill the rectangle
+                               |x| <= c1, |y| <= c2 (half-widths c1, c2) and
+                               the smooth sheet of convergence -kappa_star
+                               covers that rectangle (App. B); the ray grid
+                               must lie strictly inside it.  In FMM modes the
+                               sheet's part beyond -kappa_star z, analytic in
+                               the rectangle, joins each sub-cell's expansion
+                               (no per-ray cost); its series converges like
+                               sqrt(2) L_s / (distance to the nearest
+                               corner), and mm_create fails with MM_EINVAL
+                               where that ratio exceeds 1/2 for a sub-cell
+                               of the grid.  0 (both): stars in a disk around
+                               the origin, sheet -kappa_star z (Sec. 3.1). */
 } mm_options;
 
 /* Every derived scalar of a run (host-side numbers; no GPU needed). */

@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("col_begin", ctypes.c_int64), ("col_end", ctypes.c_int64),
                 ("no_cull", ctypes.c_int32), ("big_queue_slots", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("tune_cache", ctypes.c_char_p), ("critical_mu", ctypes.c_double)]
+                ("tune_cache", ctypes.c_char_p), ("critical_mu", ctypes.c_double),
+                ("star_rect", ctypes.c_double * 2)]
 
 
 class Params(ctypes.Structure):
@@ -170,7 +171,8 @@ def _ptr(a):
 def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=None,
                  flux_fraction_f=0.0, center_y=(0.0, 0.0), row_begin=0, row_end=0,
                  rows_per_item=0, col_begin=0, col_end=0, sub_levels=0, cull=True,
-                 big_queue_slots=0, autotune=False, tune_cache=None, critical_mu=0.0):
+                 big_queue_slots=0, autotune=False, tune_cache=None, critical_mu=0.0,
+                 star_rect=None):
     o = Options()
     o.mode = int(mode)
     o.time_stages = 1 if time_stages else 0
@@ -188,6 +190,8 @@ def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=No
     o.col_begin, o.col_end = int(col_begin), int(col_end)
     o.autotune = 1 if autotune else 0
     o.critical_mu = float(critical_mu)
+    if star_rect is not None:
+        o.star_rect[0], o.star_rect[1] = float(star_rect[0]), float(star_rect[1])
     # (the structure keeps the encoded path alive while it lives)
     o.tune_cache = os.fsencode(tune_cache) if tune_cache is not None else None
     return o

@@ -557,6 +557,10 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
   C.lox = P.center_y[0] - P.half_length;
   C.loy = P.center_y[1] - P.half_length;
   C.delta = P.delta;
+  C.x1 = P.x0[0] + (double)(P.n[0] - 1) * P.h[0];
+  C.y1 = P.x0[1] + (double)(P.n[1] - 1) * P.h[1];
+  C.rect_c1 = h->opt.star_rect[0];
+  C.rect_c2 = h->opt.star_rect[1];
   const int64_t n_rec = h->n_active << (2 * h->sub);
   LCH(launch_near_count(T, C, h->n_active, h->active_list.p, h->near_cnt.p, h->err.p, st));
   CKS(cub_call(h, plan, [&](void *tmp, size_t &bytes) {
@@ -778,6 +782,8 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     C.lox = P.center_y[0] - P.half_length;
     C.loy = P.center_y[1] - P.half_length;
     C.delta = P.delta;
+    C.rect_c1 = h->opt.star_rect[0];
+    C.rect_c2 = h->opt.star_rect[1];
     LCH(launch_direct64_vertices(h->sx.p, h->sy.p, h->sm.p, h->N, C, h->col_lo,
                                  h->col_hi - h->col_lo + 1, h->row_lo, h->row_hi, h->verts.p,
                                  st));
@@ -928,6 +934,18 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
                 "the stars' bounding box [%g, %g] x [%g, %g] does not cover the shooting "
                 "region [%g, %g] x [%g, %g]",
                 bx0, bx1, by0, by1, gx0, gx1, gy0, gy1);
+  if (h->opt.star_rect[0] != 0.0 || h->opt.star_rect[1] != 0.0) {
+    // App. B: rectangular star region centred on the origin
+    const double c1 = h->opt.star_rect[0], c2 = h->opt.star_rect[1];
+    if (!(c1 > 0.0 && c2 > 0.0 && std::isfinite(c1) && std::isfinite(c2)))
+      return fail(MM_EINVAL, "star_rect (%g, %g) must be two positive half-widths", c1, c2);
+    if (!(std::max(std::fabs(gx0), std::fabs(gx1)) < c1 &&
+          std::max(std::fabs(gy0), std::fabs(gy1)) < c2))
+      return fail(MM_EINVAL,
+                  "the shooting region [%g, %g] x [%g, %g] is not inside the star rectangle "
+                  "|x| < %g, |y| < %g",
+                  gx0, gx1, gy0, gy1, c1, c2);
+  }
   ext = std::max(ext, std::max(std::max(std::fabs(gx0), std::fabs(gx1)),
                                std::max(std::fabs(gy0), std::fabs(gy1))));
   h->R0 = std::ldexp(1.0, (int)std::ceil(std::log2(std::max(ext * 1.0001, 1e-3))));
@@ -978,6 +996,10 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
   unsigned e = 0;
   CK(cudaMemcpy(&e, h->err.p, sizeof e, cudaMemcpyDeviceToHost));
   if (e & ERR_TREE_INVARIANT) return fail(MM_ECUDA, "internal: quadtree invariant violated");
+  if (e & ERR_RECT_CORNER)
+    return fail(MM_EINVAL,
+                "a corner of star_rect lies within two half-diagonals of a ray-grid sub-cell: "
+                "widen the rectangle or use sub-cells (sub_levels 1 or 2)");
   h->last_stream = st;
   return MM_OK;
 }
@@ -1338,6 +1360,8 @@ mm_status mm_shoot_points(mm_map *h, int64_t n, const double *z_xy, double *w_xy
       C.lox = P.center_y[0] - P.half_length;
       C.loy = P.center_y[1] - P.half_length;
       C.delta = P.delta;
+      C.rect_c1 = h->opt.star_rect[0];
+      C.rect_c2 = h->opt.star_rect[1];
       e = launch_direct64_points(h->sx.p, h->sy.p, h->sm.p, h->N, C, n, dz, dw, st);
     } else {
       if (!h->prepared) {

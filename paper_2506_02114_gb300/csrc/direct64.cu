@@ -1,4 +1,5 @@
-// Plain FP64 path: the lens equation of Sec. 2.2 (circular sheet, Sec. 3.1)
+// Plain FP64 path: the lens equation of Sec. 2.2 (sheet of Sec. 3.1, or of
+// App. B for a rectangular star region)
 // summed directly over every star in FP64 for each ray vertex (no tree), then
 // the same inverse polygon mapping as the FMM path, reading the mapped
 // vertices back from a buffer.  This is the baseline the FMM path's speed-up
@@ -54,6 +55,11 @@ __device__ __forceinline__ void lens64(const DirectConst &C, double x, double y,
   const double ak = 1.0 - C.kappa + C.kappa_star;
   wx = (ak + C.gamma) * x - ax;
   wy = (ak - C.gamma) * y - ay;
+  if (C.rect_c1 > 0.0) {  // rectangular sheet (App. B): alpha_s = -kappa_star z + conj(At)
+    const double2 t = rect_sheet_At(C.kappa_star, C.rect_c1, C.rect_c2, x, y);
+    wx -= t.x;
+    wy += t.y;
+  }
 }
 
 __global__ void __launch_bounds__(D64_TILE) k_direct64_vertices(

@@ -411,6 +411,62 @@ __global__ void __launch_bounds__(64) k_leaf_finalize(TreeDev T, FmmConst C, int
         }
       },
       err);
+
+  // Rectangular star region: the sheet's part beyond -kappa_star z is the
+  // conjugate of At, analytic inside the rectangle, so its potential joins
+  // the expansion like a far source: d_n += At^(n-1)(z_q) L_q^n / n!, with
+  //   At'    = (kappa_star i / pi) sum_a s_a (-log(a - z)) - kappa_star,
+  //   At^(k) = (kappa_star i / pi) sum_a s_a (k - 2)! / (a - z)^(k - 1), k >= 2,
+  // i.e. d_n += (kappa_star i / pi) L_q^2 sum_a s_a r_a^(n-2) / (n (n-1) (n-2))
+  // for n >= 3, r_a = L_q / (a - z_q).  No per-ray cost.
+  if (C.rect_c1 > 0.0) {
+    const double2 t0 = rect_sheet_At(C.kappa_star, C.rect_c1, C.rect_c2, cx, cy);
+    d1.x += t0.x * Lq;
+    d1.y += t0.y * Lq;
+    const double f = C.kappa_star / 3.14159265358979323846;
+    double lx = 0.0, ly = 0.0, rx[4], ry[4], px[4], py[4], sg[4], dmin2 = 1e300;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      double ax, ay;
+      rect_corner(C.rect_c1, C.rect_c2, k, ax, ay, sg[k]);
+      const double dx = ax - cx, dy = ay - cy, q = Lq / (dx * dx + dy * dy);
+      dmin2 = fmin(dmin2, dx * dx + dy * dy);
+      const double2 l = clog64(dx, dy);
+      lx -= sg[k] * l.x;
+      ly -= sg[k] * l.y;
+      rx[k] = dx * q;   // L_q / (a - z_q)
+      ry[k] = -dy * q;
+      px[k] = 1.0;      // r_a^(n-2)
+      py[k] = 0.0;
+    }
+    // the series converges like sqrt(2) L_q / (distance to the nearest
+    // corner) over the record; beyond 1/2 its truncation is not negligible
+    // (only sub-cells meeting the ray grid are ever evaluated)
+    const bool on_grid = cx + Lq >= C.x0 && cx - Lq <= C.x1 && cy + Lq >= C.y0 && cy - Lq <= C.y1;
+    if (on_grid && 2.0 * Lq * Lq > 0.25 * dmin2) atomicOr(err, ERR_RECT_CORNER);
+    const double l2 = Lq * Lq;
+    if (pe >= 2) {
+      d[2].x += (float)((-f * ly - C.kappa_star) * l2 * 0.5);
+      d[2].y += (float)(f * lx * l2 * 0.5);
+    }
+#pragma unroll
+    for (int n = 3; n <= NB; n++) {
+      double sx = 0.0, sy = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const double t = px[k] * rx[k] - py[k] * ry[k];
+        py[k] = px[k] * ry[k] + py[k] * rx[k];
+        px[k] = t;
+        sx += sg[k] * px[k];
+        sy += sg[k] * py[k];
+      }
+      if (n <= pe) {
+        const double w = f * l2 / ((double)n * (n - 1) * (n - 2));  // times i
+        d[n].x += (float)(-w * sy);
+        d[n].y += (float)(w * sx);
+      }
+    }
+  }
   R.near_off = near_off[g];
   R.near_cnt = (int32_t)(k - R.near_off);
 

@@ -26,6 +26,8 @@ namespace mm {
 enum : unsigned int {
   ERR_TREE_INVARIANT = 1u,    // a split node lacks a same-level neighbour
   ERR_LOOKUP = 2u,            // a ray vertex fell outside every active leaf
+  ERR_RECT_CORNER = 4u,       // a record's rectangular-sheet series converges too
+                              // slowly (a star-rectangle corner is near it)
 };
 
 // Per sub-cell of an active leaf: everything a ray vertex in it needs (64
@@ -152,6 +154,50 @@ __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *a, int64_t lo
       hi = mid;
   }
   return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Smooth sheet of a rectangular star region (App. B).  For the sheet of
+// convergence -kappa_star on |x| <= c1, |y| <= c2 and a point z inside it,
+// alpha_s(z) = -kappa_star z + A(z) with
+//   A(z)  = (-kappa_star i / pi) F(conj z) - kappa_star (2 c1 + conj z),
+//   F(t)  = f_c(t) - f_cb(t) + f_-c(t) - f_-cb(t),   f_a(t) = (a - t) log(a - t),
+// c = c1 + i c2, cb = conj c, principal logarithms (no branch cut meets the
+// interior).  A depends on conj z alone, so At(z) = conj A(z) is analytic
+// inside:  At(z) = (kappa_star i / pi) G(z) - kappa_star (2 c1 + z) with
+// G = f_cb - f_c + f_-cb - f_-c; the -kappa_star z part stays in the macro
+// factor 1 - kappa + kappa_star, exactly as for a star disk.
+// ---------------------------------------------------------------------------
+
+// the four corners a of G and their signs: cb (+), c (-), -cb (+), -c (-)
+__device__ __forceinline__ void rect_corner(double c1, double c2, int k, double &ax, double &ay,
+                                            double &sgn) {
+  ax = (k < 2) ? c1 : -c1;
+  ay = (k & 1) ? c2 : -c2;
+  if (k >= 2) ay = -ay;  // -cb = -c1 + i c2, -c = -c1 - i c2
+  sgn = (k & 1) ? -1.0 : 1.0;
+}
+
+// principal log of x + i y
+__device__ __forceinline__ double2 clog64(double x, double y) {
+  return make_double2(log(hypot(x, y)), atan2(y, x));
+}
+
+// At(z) inside the rectangle (the value; A(z) = conj of it)
+__device__ __forceinline__ double2 rect_sheet_At(double ks, double c1, double c2, double x,
+                                                 double y) {
+  double gx = 0.0, gy = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    double ax, ay, sg;
+    rect_corner(c1, c2, k, ax, ay, sg);
+    const double dx = ax - x, dy = ay - y;  // a - z
+    const double2 l = clog64(dx, dy);
+    gx += sg * (dx * l.x - dy * l.y);
+    gy += sg * (dx * l.y + dy * l.x);
+  }
+  const double f = ks / 3.14159265358979323846;  // (kappa_star i / pi) G
+  return make_double2(-f * gy - ks * (2.0 * c1 + x), f * gx - ks * y);
 }
 
 }  // namespace mm

@@ -64,7 +64,9 @@ struct FmmConst {
   int cull;                   // 1: compute the culling bounds
   double kappa, gamma, kappa_star;
   double x0, y0, hx, hy;      // ray grid
+  double x1, y1;              // the grid's last vertex
   double lox, loy, delta;     // map lower-left corner and pixel side
+  double rect_c1, rect_c2;    // > 0: rectangular star region |x| <= c1, |y| <= c2 (App. B)
 };
 
 cudaError_t launch_p2m(const TreeDev &T, int64_t n_nodes, int p, double2 *mp, cudaStream_t st);
@@ -109,6 +111,7 @@ struct DirectConst {
   double kappa, gamma, kappa_star;
   double x0, y0, hx, hy;
   double lox, loy, delta;
+  double rect_c1, rect_c2;    // > 0: rectangular star region (App. B); 0: disk
 };
 // vertices of columns [col0, col0 + width) and rows [row_lo, row_hi], row-major
 cudaError_t launch_direct64_vertices(const double *sx, const double *sy, const double *sm,

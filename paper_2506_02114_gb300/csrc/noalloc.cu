@@ -131,6 +131,7 @@ extern "C" mm_status mm_map_plain_fp64_noalloc(
   C.lox = cx - half_length;
   C.loy = cy - half_length;
   C.delta = delta;
+  C.rect_c1 = C.rect_c2 = 0.0;  // star disk
 
   MapDev md;
   memset(&md, 0, sizeof md);

@@ -127,3 +127,13 @@ def test_autotune_options_reach_the_structure():
     assert o.autotune == 1 and o.tune_cache == b"tune.jsonl"
     o = mm.make_options()
     assert o.autotune == 0 and o.tune_cache is None
+
+
+def test_create_rejects_a_bad_star_rectangle():
+    """star_rect must hold two positive half-widths enclosing the shooting
+    region (checked before any GPU call)."""
+    m, pos = synthetic.star_field_rect(3, 200, (30.0, 30.0))
+    for rect in ((-1.0, 30.0), (30.0, 0.5), (float("nan"), 30.0)):
+        with pytest.raises(mm.MMError) as e:
+            mm.create(0.3, 0.1, 0.0, m, pos, 1.0, 16, 1.0, star_rect=rect)
+        assert e.value.status == mm.MM_EINVAL
