@@ -412,3 +412,27 @@ def test_map_centre_offset(oracle_mod):
                      flux_fraction_f=0.01, center_y=cy)
     assert st["params"]["n"] == list(p.n)
     assert_map_parity(mu, mu_ref, p.mu_macro)
+
+
+@pytest.mark.parametrize("mode", [mm.MM_FMM_FP32, mm.MM_PLAIN_FP64])
+def test_star_on_a_grid_vertex(oracle_mod, mode):
+    """A star exactly on a ray vertex: that ray's deflection is infinite, and
+    the six triangles sharing the vertex are dropped (counted) by both
+    implementations; the rest of the map still meets the tolerances.  The
+    grid is dyadic (h = 1/64, origin -(4, 16)) so that the vertex and the
+    star coincide exactly on both sides."""
+    kappa, gamma, s, hl, npix = 0.45, 0.3, 0.4, 1.5, 64
+    m, pos = small_field(7, kappa, gamma, s, hl, npix, 10.0)
+    g = dict(img_half=(4.0, 16.0), ray_grid=(513, 2049))
+    m2 = np.concatenate([m, [0.5]])
+    p = oracle_inputs(oracle_mod, kappa, gamma, s, m2, hl, npix, 0.0, flux_fraction_f=0.01, **g)
+    assert p.h[0] == p.h[1] == 1.0 / 64 and p.x0[0] == -4.0 and p.x0[1] == -16.0
+    v = oracle_mod.grid_vertices(p, [300], [900])
+    pos2 = np.concatenate([pos, v])
+    assert not np.isfinite(oracle_mod.deflect(p, m2, pos2, v)).all()
+    mu_ref, st_ref = oracle_mod.magnification_map(p, m2, pos2)
+    assert st_ref["dropped"] == 6
+    mu, st = gpu_map(kappa, gamma, s, m2, pos2, hl, npix, fmm_order=25, mode=mode,
+                     flux_fraction_f=0.01, **g)
+    assert st["triangles_dropped"] == 6
+    assert_map_parity(mu, mu_ref, p.mu_macro)
