@@ -36,11 +36,11 @@ class Params(ctypes.Structure):
         ("mu_macro", ctypes.c_double), ("mean_m", ctypes.c_double),
         ("m2_over_m", ctypes.c_double), ("flux_fraction_f", ctypes.c_double),
         ("r_border", ctypes.c_double), ("half_length", ctypes.c_double),
-        ("npix", ctypes.c_int32), ("delta", ctypes.c_double),
+        ("npix", ctypes.c_int32), ("npix_y", ctypes.c_int32), ("delta", ctypes.c_double),
         ("center_y", ctypes.c_double * 2), ("img_center", ctypes.c_double * 2),
         ("img_half", ctypes.c_double * 2), ("n", ctypes.c_int64 * 2),
         ("h", ctypes.c_double * 2), ("x0", ctypes.c_double * 2),
-        ("star_rect", ctypes.c_double * 2),
+        ("star_rect", ctypes.c_double * 2), ("half_length_y", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -67,7 +67,7 @@ def lib():
         L.or_derive_params.restype = ctypes.c_int
         L.or_derive_params.argtypes = [
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64, _dp,
-            ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _dp,
+            ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _dp,
             _dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(Params)]
         L.or_alpha_rect.restype = None
         L.or_alpha_rect.argtypes = [ctypes.POINTER(Params), ctypes.c_double, ctypes.c_double,
@@ -113,7 +113,7 @@ def default_threads():
 
 def derive_params(kappa, gamma, smooth_fraction, masses, half_length, npix,
                   rays_per_pixel=0.0, flux_fraction_f=0.0, center_y=None,
-                  img_half=None, ray_grid=None, star_rect=None) -> Params:
+                  img_half=None, ray_grid=None, star_rect=None, npix_y=0) -> Params:
     m = _f64(masses)
     p = Params()
     cy = _f64(center_y) if center_y is not None else None
@@ -122,7 +122,8 @@ def derive_params(kappa, gamma, smooth_fraction, masses, half_length, npix,
           if ray_grid is not None else None)
     rc = lib().or_derive_params(
         float(kappa), float(gamma), float(smooth_fraction), m.size, _ptr(m),
-        float(half_length), int(npix), float(rays_per_pixel), float(flux_fraction_f),
+        float(half_length), int(npix), int(npix_y), float(rays_per_pixel),
+        float(flux_fraction_f),
         _ptr(cy), _ptr(ih),
         rg.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if rg is not None else None,
         ctypes.byref(p))
@@ -164,9 +165,9 @@ def magnification_map(params: Params, masses, pos_xy, row_begin=0, row_end=0,
     """Magnification map (npix, npix) from the cell rows [row_begin, row_end)."""
     m = _f64(masses)
     xy = _f64(pos_xy).reshape(-1, 2)
-    n = params.npix
-    mu = np.zeros((n, n), dtype=np.float64)
-    acc = np.zeros((n, n), dtype=np.float64)
+    n, ny = params.npix, params.npix_y
+    mu = np.zeros((ny, n), dtype=np.float64)
+    acc = np.zeros((ny, n), dtype=np.float64)
     st = MapStats()
     rc = lib().or_map(ctypes.byref(params), m.size, _ptr(m), _ptr(xy), int(row_begin),
                       int(row_end), mu.ctypes.data_as(_dp), acc.ctypes.data_as(_dp),
@@ -183,9 +184,9 @@ def magnification_map_tile(params: Params, masses, pos_xy, row_begin, row_end, c
     [col_begin, col_end) of the ray grid."""
     m = _f64(masses)
     xy = _f64(pos_xy).reshape(-1, 2)
-    n = params.npix
-    mu = np.zeros((n, n), dtype=np.float64)
-    acc = np.zeros((n, n), dtype=np.float64)
+    n, ny = params.npix, params.npix_y
+    mu = np.zeros((ny, n), dtype=np.float64)
+    acc = np.zeros((ny, n), dtype=np.float64)
     st = MapStats()
     rc = lib().or_map_tile(ctypes.byref(params), m.size, _ptr(m), _ptr(xy), int(row_begin),
                            int(row_end), int(col_begin), int(col_end), mu.ctypes.data_as(_dp),
@@ -200,9 +201,9 @@ def map_from_vertices(params: Params, w_xy, row_begin, row_end, nthreads=None):
     """IPM only: map from source positions of the vertices of rows
     [row_begin, row_end] (inclusive)."""
     w = _f64(w_xy).reshape(-1, 2)
-    n = params.npix
-    mu = np.zeros((n, n), dtype=np.float64)
-    acc = np.zeros((n, n), dtype=np.float64)
+    n, ny = params.npix, params.npix_y
+    mu = np.zeros((ny, n), dtype=np.float64)
+    acc = np.zeros((ny, n), dtype=np.float64)
     st = MapStats()
     rc = lib().or_map_from_vertices(ctypes.byref(params), _ptr(w), int(row_begin),
                                     int(row_end), mu.ctypes.data_as(_dp),
@@ -220,9 +221,9 @@ def irs_map(params: Params, masses, pos_xy, row_begin=0, row_end=-1, col_begin=0
     (mu, counts (npix, npix) int64, dropped)."""
     m = _f64(masses)
     xy = _f64(pos_xy).reshape(-1, 2)
-    n = params.npix
-    mu = np.zeros((n, n), dtype=np.float64)
-    cnt = np.zeros((n, n), dtype=np.int64)
+    n, ny = params.npix, params.npix_y
+    mu = np.zeros((ny, n), dtype=np.float64)
+    cnt = np.zeros((ny, n), dtype=np.int64)
     dropped = ctypes.c_int64(0)
     rc = lib().or_irs_tile(ctypes.byref(params), m.size, _ptr(m), _ptr(xy), int(row_begin),
                            int(row_end), int(col_begin), int(col_end),

@@ -21,12 +21,13 @@
 
 int or_derive_params(double kappa, double gamma, double smooth_fraction,
                      int64_t n_stars, const double *masses,
-                     double half_length, int32_t npix, double rays_per_pixel,
+                     double half_length, int32_t npix, int32_t npix_y,
+                     double rays_per_pixel,
                      double flux_fraction_f, const double *center_y,
                      const double *img_half_opt, const int64_t *ray_grid_opt,
                      or_params *out) {
   memset(out, 0, sizeof(*out));
-  if (!(half_length > 0) || npix < 1) return -1;
+  if (!(half_length > 0) || npix < 1 || npix_y < 0) return -1;
   if (!(smooth_fraction >= 0 && smooth_fraction <= 1)) return -1;
   out->kappa = kappa;
   out->gamma = gamma;
@@ -55,7 +56,10 @@ int or_derive_params(double kappa, double gamma, double smooth_fraction,
 
   out->half_length = half_length;
   out->npix = npix;
+  out->npix_y = npix_y > 0 ? npix_y : npix;
   out->delta = 2.0 * half_length / (double)npix;
+  /* square pixels: the map is npix_y delta high */
+  out->half_length_y = out->npix_y == npix ? half_length : 0.5 * out->npix_y * out->delta;
   out->center_y[0] = center_y ? center_y[0] : 0.0;
   out->center_y[1] = center_y ? center_y[1] : 0.0;
 
@@ -69,7 +73,7 @@ int or_derive_params(double kappa, double gamma, double smooth_fraction,
     out->img_half[1] = img_half_opt[1];
   } else {
     out->img_half[0] = (half_length + out->r_border) / fabs(out->a1);
-    out->img_half[1] = (half_length + out->r_border) / fabs(out->a2);
+    out->img_half[1] = (out->half_length_y + out->r_border) / fabs(out->a2);
   }
 
   /* Ray grid (Sec. 3.2, Table 1 caption): rays_per_pixel counts rays per
@@ -282,13 +286,13 @@ typedef struct {
   int64_t vrow0;
   int64_t col0, col1; /* cell columns [col0, col1) */
   int64_t crow_begin, crow_end; /* cell rows handled by this worker */
-  double *acc;                  /* npix*npix partial sums */
+  double *acc;                  /* npix_y*npix partial sums */
   or_map_stats st;
 } map_job;
 
 /* One triangle with vertices already in pixel units: every pixel of its
  * bounding box (within the map) gets area(T n pixel) / |area(T)|. */
-static void apportion_triangle(const double *tri, int npix, double *acc,
+static void apportion_triangle(const double *tri, int npix, int npix_y, double *acc,
                                or_map_stats *st) {
   st->triangles++;
   for (int k = 0; k < 6; k++)
@@ -301,7 +305,7 @@ static void apportion_triangle(const double *tri, int npix, double *acc,
   double ymin = fmin(tri[1], fmin(tri[3], tri[5]));
   double ymax = fmax(tri[1], fmax(tri[3], tri[5]));
   /* wholly outside the map: nothing to apportion (not counted as dropped) */
-  if (xmax < 0 || ymax < 0 || xmin >= npix || ymin >= npix) return;
+  if (xmax < 0 || ymax < 0 || xmin >= npix || ymin >= npix_y) return;
   double area_t = shoelace(tri, 3);
   if (area_t == 0.0) {
     st->dropped++;
@@ -312,7 +316,7 @@ static void apportion_triangle(const double *tri, int npix, double *acc,
   if (px0 < 0) px0 = 0;
   if (py0 < 0) py0 = 0;
   if (px1 > npix - 1) px1 = npix - 1;
-  if (py1 > npix - 1) py1 = npix - 1;
+  if (py1 > npix_y - 1) py1 = npix_y - 1;
   for (int64_t py = py0; py <= py1; py++)
     for (int64_t px = px0; px <= px1; px++) {
       double a = or_tri_rect_area(tri, (double)px, (double)py,
@@ -330,7 +334,7 @@ static void *map_worker(void *arg) {
   int64_t width = J->col1 - J->col0 + 1; /* vertices per stored row */
   double inv = 1.0 / p->delta;
   double lo0 = p->center_y[0] - p->half_length;
-  double lo1 = p->center_y[1] - p->half_length;
+  double lo1 = p->center_y[1] - p->half_length_y;
   for (int64_t j = J->crow_begin; j < J->crow_end; j++) {
     const double *r0 = J->w_xy + 2 * (j - J->vrow0) * width - 2 * J->col0;
     const double *r1 = r0 + 2 * width;
@@ -343,8 +347,8 @@ static void *map_worker(void *arg) {
       /* two triangles split along the v00-v11 diagonal */
       double t1[6] = {v00[0], v00[1], v10[0], v10[1], v11[0], v11[1]};
       double t2[6] = {v00[0], v00[1], v11[0], v11[1], v01[0], v01[1]};
-      apportion_triangle(t1, p->npix, J->acc, &J->st);
-      apportion_triangle(t2, p->npix, J->acc, &J->st);
+      apportion_triangle(t1, p->npix, p->npix_y, J->acc, &J->st);
+      apportion_triangle(t2, p->npix, p->npix_y, J->acc, &J->st);
     }
   }
   return NULL;
@@ -360,7 +364,7 @@ static int map_tile_from_vertices(const or_params *p, const double *w_xy,
   if (nthreads > 256) nthreads = 256;
   int64_t rows = row_end - row_begin;
   if (nthreads > rows) nthreads = (int)rows;
-  size_t npx = (size_t)p->npix * (size_t)p->npix;
+  size_t npx = (size_t)p->npix * (size_t)p->npix_y;
   double *part = (double *)calloc(npx * (size_t)nthreads, sizeof(double));
   if (!part) return -1;
   map_job jobs[256];
@@ -458,7 +462,7 @@ int or_irs_tile(const or_params *p, int64_t n_stars, const double *masses,
   int64_t width = col_end - col_begin + 1;
   int64_t nv = (row_end - row_begin + 1) * width;
   double *w = (double *)malloc((size_t)nv * 2 * sizeof(double));
-  size_t npx = (size_t)p->npix * (size_t)p->npix;
+  size_t npx = (size_t)p->npix * (size_t)p->npix_y;
   int64_t *cnt = (int64_t *)calloc(npx, sizeof(int64_t));
   if (!w || !cnt) {
     free(w);
@@ -467,7 +471,7 @@ int or_irs_tile(const or_params *p, int64_t n_stars, const double *masses,
   }
   run_deflect(p, n_stars, masses, pos_xy, nv, NULL, row_begin, col_begin, width, w, nthreads);
   /* each ray counts once, in the pixel its source position lies in */
-  const double lox = p->center_y[0] - p->half_length, loy = p->center_y[1] - p->half_length;
+  const double lox = p->center_y[0] - p->half_length, loy = p->center_y[1] - p->half_length_y;
   int64_t nd = 0;
   for (int64_t k = 0; k < nv; k++) {
     double wx = w[2 * k], wy = w[2 * k + 1];
@@ -476,7 +480,7 @@ int or_irs_tile(const or_params *p, int64_t n_stars, const double *masses,
       continue;
     }
     double u = floor((wx - lox) / p->delta), v = floor((wy - loy) / p->delta);
-    if (u >= 0 && u < p->npix && v >= 0 && v < p->npix)
+    if (u >= 0 && u < p->npix && v >= 0 && v < p->npix_y)
       cnt[(size_t)v * (size_t)p->npix + (size_t)u]++;
   }
   double scale = p->h[0] * p->h[1] / (p->delta * p->delta);

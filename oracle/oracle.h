@@ -50,8 +50,9 @@ typedef struct {
   double flux_fraction_f;     /* App. A, default 1e-3 */
   double r_border;            /* theta_star sqrt(kappa_star <m^2>/(f <m>)), App. A */
   /* source-plane map (square, Sec. 2.3) */
-  double half_length;
-  int32_t npix;
+  double half_length;         /* half-width (x) of the map */
+  int32_t npix;               /* pixels along x */
+  int32_t npix_y;             /* pixels along y (square pixels) */
   double delta;               /* pixel side 2 half_length / npix */
   double center_y[2];
   /* image-plane shooting region (Sec. 2.3) and ray grid (Sec. 3.2) */
@@ -64,6 +65,7 @@ typedef struct {
    * convergence -kappa_star on the rectangle |x| <= c1, |y| <= c2 (App. B);
    * zeros (the default) on the disk holding the stars (footnote of Sec. 3.1) */
   double star_rect[2];
+  double half_length_y;       /* half-height of the map: npix_y delta / 2 */
 } or_params;
 
 typedef struct {
@@ -75,10 +77,13 @@ typedef struct {
 
 /* Derive every scalar of the run.  img_half_opt / ray_grid_opt may be NULL
  * (or hold zeros) to take the derived values; center_y may be NULL (origin).
+ * The map is npix (x) by npix_y (y) square pixels of side 2 half_length /
+ * npix; npix_y = 0 means npix (a square map).
  * Returns 0 on success, -1 on invalid arguments. */
 int or_derive_params(double kappa, double gamma, double smooth_fraction,
                      int64_t n_stars, const double *masses,
-                     double half_length, int32_t npix, double rays_per_pixel,
+                     double half_length, int32_t npix, int32_t npix_y,
+                     double rays_per_pixel,
                      double flux_fraction_f, const double *center_y,
                      const double *img_half_opt, const int64_t *ray_grid_opt,
                      or_params *out);
@@ -92,7 +97,7 @@ void or_deflect(const or_params *p, int64_t n_stars, const double *masses,
                 const double *pos_xy, int64_t n, const double *z_xy,
                 double *w_xy, int nthreads);
 
-/* Magnification map (npix*npix, row-major, row = y pixel index) from the cell
+/* Magnification map (npix_y rows of npix, row = y pixel index) from the cell
  * rows [row_begin, row_end) of the ray grid (row_end <= 0 means all rows).
  * mu_out receives the magnification; acc_out (may be NULL) the raw sum of
  * area fractions per pixel.  Returns 0 on success. */

@@ -481,3 +481,35 @@ def test_rect_sheet_compensates_star_mass(oracle_mod):
     mean = nets.mean(0)
     sem = nets.std(0) / math.sqrt(len(nets))
     assert np.all(np.abs(mean) < 4 * sem + 0.05), (mean, sem)
+
+
+def test_non_square_map(oracle_mod):
+    """A map of npix x npix_y square pixels (side 2 half_length / npix): its
+    half-height is npix_y delta / 2, the shooting region's y half-width is
+    (that + r) / |a2| (Sec. 2.3); with no stars every covered pixel has
+    |mu_macro| (IPM), and the rays per pixel are exact lattice counts (IRS)."""
+    from fractions import Fraction as Fr
+    kappa, gamma, hl, nx, ny = 0.25, 0.125, 2.0, 16, 6
+    p = oracle_mod.derive_params(kappa, gamma, 1.0, [], hl, nx, rays_per_pixel=5.0, npix_y=ny)
+    assert (p.npix, p.npix_y) == (nx, ny) and p.half_length_y == 0.5 * ny * p.delta
+    assert abs(p.img_half[1] - (p.half_length_y + p.r_border) / abs(p.a2)) < 1e-14
+    mu, st = oracle_mod.magnification_map(p, [], np.zeros((0, 2)))
+    assert mu.shape == (ny, nx) and st["dropped"] == 0
+    np.testing.assert_allclose(mu, abs(p.mu_macro), rtol=1e-11)
+    # IRS on a dyadic grid: per-axis lattice counts, exactly
+    q = oracle_mod.derive_params(kappa, gamma, 1.0, [], hl, nx, img_half=(2.5, 3.5),
+                                 ray_grid=(41, 57), npix_y=ny)
+    _, cnt, _ = oracle_mod.irs_map(q, [], np.zeros((0, 2)))
+    delta, hy = Fr(2 * hl) / nx, Fr(ny) * Fr(2 * hl) / nx / 2
+
+    def axis(a, half, n, lo, npx):
+        c = np.zeros(npx, dtype=np.int64)
+        for i in range(n):
+            k = math.floor((Fr(a) * (-Fr(half) + i * Fr(2 * half) / (n - 1)) - lo) / delta)
+            if 0 <= k < npx:
+                c[k] += 1
+        return c
+
+    cx = axis(1 - kappa + gamma, 2.5, 41, -Fr(hl), nx)
+    cy = axis(1 - kappa - gamma, 3.5, 57, -hy, ny)
+    np.testing.assert_array_equal(cnt, np.outer(cy, cx))
