@@ -155,6 +155,10 @@ typedef struct {
                                where that ratio exceeds 1/2 for a sub-cell
                                of the grid.  0 (both): stars in a disk around
                                the origin, sheet -kappa_star z (Sec. 3.1). */
+  int32_t npix_y;           /* > 0: the map has npix_y rows of npix square
+                               pixels of side 2 half_length / npix (half-height
+                               npix_y delta / 2); 0: npix rows (square map) */
+  int32_t reserved1;        /* 0 */
 } mm_options;
 
 /* Every derived scalar of a run (host-side numbers; no GPU needed). */
@@ -167,15 +171,16 @@ typedef struct {
   double flux_fraction_f;
   double r_border;          /* sqrt(kappa_star <m^2> / (f <m>)), App. A */
   double half_length;
-  int32_t npix;
-  int32_t pad0;
-  double delta;             /* pixel side */
+  int32_t npix;             /* pixels along x */
+  int32_t npix_y;           /* pixels along y (square pixels) */
+  double delta;             /* pixel side 2 half_length / npix */
   double center_y[2];
   double img_center[2];     /* centre of the shooting region, Sec. 2.3 */
   double img_half[2];       /* half-widths of the shooting region */
   int64_t n[2];             /* rays (grid vertices) per axis */
   double h[2];              /* ray spacing per axis */
   double x0[2];             /* image-plane position of vertex (0, 0) */
+  double half_length_y;     /* half-height of the map, npix_y delta / 2 */
 } mm_params;
 
 typedef struct {

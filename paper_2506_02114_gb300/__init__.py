@@ -11,7 +11,7 @@ Typical use::
     h = mm.create(kappa, gamma, s, masses, pos, half_length, npix,
                   rays_per_pixel=9.0, fmm_order=25)
     mm.run(h)                  # on torch's current CUDA stream
-    mu = mm.get_map(h)         # numpy (npix, npix) float32, row = y
+    mu = mm.get_map(h)         # numpy (npix_y, npix) float32, row = y
     mm.destroy(h)
 """
 import ctypes
@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
                 ("no_cull", ctypes.c_int32), ("big_queue_slots", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("tune_cache", ctypes.c_char_p), ("critical_mu", ctypes.c_double),
-                ("star_rect", ctypes.c_double * 2)]
+                ("star_rect", ctypes.c_double * 2), ("npix_y", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -53,15 +54,15 @@ class Params(ctypes.Structure):
                 ("mu_macro", ctypes.c_double), ("mean_m", ctypes.c_double),
                 ("m2_over_m", ctypes.c_double), ("flux_fraction_f", ctypes.c_double),
                 ("r_border", ctypes.c_double), ("half_length", ctypes.c_double),
-                ("npix", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("npix", ctypes.c_int32), ("npix_y", ctypes.c_int32),
                 ("delta", ctypes.c_double), ("center_y", ctypes.c_double * 2),
                 ("img_center", ctypes.c_double * 2), ("img_half", ctypes.c_double * 2),
                 ("n", ctypes.c_int64 * 2), ("h", ctypes.c_double * 2),
-                ("x0", ctypes.c_double * 2)]
+                ("x0", ctypes.c_double * 2), ("half_length_y", ctypes.c_double)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if hasattr(getattr(self, k), "__len__")
-                    else getattr(self, k)) for k, _ in self._fields_ if k != "pad0"}
+                    else getattr(self, k)) for k, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -172,7 +173,7 @@ def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=No
                  flux_fraction_f=0.0, center_y=(0.0, 0.0), row_begin=0, row_end=0,
                  rows_per_item=0, col_begin=0, col_end=0, sub_levels=0, cull=True,
                  big_queue_slots=0, autotune=False, tune_cache=None, critical_mu=0.0,
-                 star_rect=None):
+                 star_rect=None, npix_y=0):
     o = Options()
     o.mode = int(mode)
     o.time_stages = 1 if time_stages else 0
@@ -192,6 +193,7 @@ def make_options(mode=MM_FMM_FP32, time_stages=False, img_half=None, ray_grid=No
     o.critical_mu = float(critical_mu)
     if star_rect is not None:
         o.star_rect[0], o.star_rect[1] = float(star_rect[0]), float(star_rect[1])
+    o.npix_y = int(npix_y)
     # (the structure keeps the encoded path alive while it lives)
     o.tune_cache = os.fsencode(tune_cache) if tune_cache is not None else None
     return o
@@ -212,9 +214,10 @@ def derive_params(kappa, gamma, s, masses, half_length, npix, rays_per_pixel=0.0
 class Handle:
     """Owns an mm_map*; destroyed explicitly or when garbage collected."""
 
-    def __init__(self, ptr, npix):
+    def __init__(self, ptr, npix, npix_y=None):
         self.ptr = ptr
         self.npix = npix
+        self.npix_y = npix_y or npix
 
     def __del__(self):
         try:
@@ -234,7 +237,7 @@ def create(kappa, gamma, s, masses, pos_xy, half_length, npix, rays_per_pixel=0.
     _check(lib().mm_create(float(kappa), float(gamma), float(s), m.size, _ptr(m), _ptr(pos),
                            float(half_length), int(npix), float(rays_per_pixel),
                            int(fmm_order), int(leaf_size), ctypes.byref(o), ctypes.byref(out)))
-    return Handle(out, int(npix))
+    return Handle(out, int(npix), int(o.npix_y) or int(npix))
 
 
 def current_stream():
@@ -259,19 +262,19 @@ def run_batch(hs, stream=None):
 
 
 def get_map(h: Handle, out=None):
-    """Magnification map.  out=None: new numpy (npix, npix) float32 array.
-    out may be a torch CUDA float32 tensor with npix*npix elements."""
+    """Magnification map.  out=None: new numpy (npix_y, npix) float32 array.
+    out may be a torch CUDA float32 tensor with npix_y*npix elements."""
     if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
         _check(lib().mm_get_map(h.ptr, _vp(out.data_ptr()), 1))
         return out
-    a = np.empty((h.npix, h.npix), dtype=np.float32) if out is None else out
+    a = np.empty((h.npix_y, h.npix), dtype=np.float32) if out is None else out
     _check(lib().mm_get_map(h.ptr, a.ctypes.data_as(_vp), 0))
     return a
 
 
 def get_map_fixed(h: Handle):
-    """Raw fixed-point accumulator (npix, npix) uint64: sum of round(frac*2^32)."""
-    a = np.empty((h.npix, h.npix), dtype=np.uint64)
+    """Raw fixed-point accumulator (npix_y, npix) uint64: sum of round(frac*2^32)."""
+    a = np.empty((h.npix_y, h.npix), dtype=np.uint64)
     _check(lib().mm_get_map_fixed(h.ptr, a.ctypes.data_as(_vp), 0))
     return a
 

@@ -254,6 +254,7 @@ static mm_status derive(double kappa, double gamma, double s, int64_t n_stars,
   if (!(s >= 0.0 && s <= 1.0)) return fail(MM_EINVAL, "smooth_fraction %g outside [0, 1]", s);
   if (!(half_length > 0.0)) return fail(MM_EINVAL, "half_length must be > 0");
   if (npix < 1) return fail(MM_EINVAL, "npix must be >= 1");
+  if (o.npix_y < 0) return fail(MM_EINVAL, "npix_y must be >= 0");
   if (n_stars < 0) return fail(MM_EINVAL, "n_stars must be >= 0");
   if (n_stars > 0 && !masses) return fail(MM_EINVAL, "masses is NULL");
   const double detm = (1.0 - kappa) * (1.0 - kappa) - gamma * gamma;
@@ -282,7 +283,10 @@ static mm_status derive(double kappa, double gamma, double s, int64_t n_stars,
   P.r_border = std::sqrt(P.kappa_star * P.m2_over_m / P.flux_fraction_f);
   P.half_length = half_length;
   P.npix = npix;
+  P.npix_y = o.npix_y > 0 ? o.npix_y : npix;
   P.delta = 2.0 * half_length / (double)npix;
+  // square pixels: the map is npix_y delta high
+  P.half_length_y = P.npix_y == npix ? half_length : 0.5 * (double)P.npix_y * P.delta;
   P.center_y[0] = o.center_y[0];
   P.center_y[1] = o.center_y[1];
   // Sec. 2.3: the macro image of the map, widened by the border r
@@ -291,7 +295,7 @@ static mm_status derive(double kappa, double gamma, double s, int64_t n_stars,
     P.img_center[k] = P.center_y[k] / a[k];
     P.img_half[k] = (o.img_half[0] > 0.0 && o.img_half[1] > 0.0)
                         ? o.img_half[k]
-                        : (half_length + P.r_border) / std::fabs(a[k]);
+                        : ((k ? P.half_length_y : half_length) + P.r_border) / std::fabs(a[k]);
   }
   const bool grid_given = o.ray_grid[0] >= 2 && o.ray_grid[1] >= 2;
   for (int k = 0; k < 2; k++) {
@@ -546,6 +550,7 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
   C.p_eval = h->p_eval;
   C.sub = h->sub;
   C.npix = P.npix;
+  C.npix_y = P.npix_y;
   C.cull = h->opt.no_cull ? 0 : 1;
   C.kappa = P.kappa;
   C.gamma = P.gamma;
@@ -555,7 +560,7 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
   C.hx = P.h[0];
   C.hy = P.h[1];
   C.lox = P.center_y[0] - P.half_length;
-  C.loy = P.center_y[1] - P.half_length;
+  C.loy = P.center_y[1] - P.half_length_y;
   C.delta = P.delta;
   C.x1 = P.x0[0] + (double)(P.n[0] - 1) * P.h[0];
   C.y1 = P.x0[1] + (double)(P.n[1] - 1) * P.h[1];
@@ -676,6 +681,7 @@ static void fill_mapdev(mm_map *h) {
   M.crit_area2 = (float)(P.h[0] * P.h[1] / (P.delta * P.delta) /
                          (h->opt.critical_mu > 0.0 ? h->opt.critical_mu : 1e3));
   M.npix = P.npix;
+  M.npix_y = P.npix_y;
   M.acc = h->acc.p;
   M.span = h->span.p;
   M.stat = h->stat.p;
@@ -685,9 +691,9 @@ static void fill_mapdev(mm_map *h) {
 }
 
 static mm_status clear_map(mm_map *h, cudaStream_t st) {
-  const size_t np = (size_t)h->P.npix * h->P.npix;
+  const size_t np = (size_t)h->P.npix * h->P.npix_y;
   CK(cudaMemsetAsync(h->acc.p, 0, np * sizeof(unsigned long long), st));
-  CK(cudaMemsetAsync(h->span.p, 0, (size_t)h->P.npix * (h->P.npix + 1) * sizeof(unsigned long long),
+  CK(cudaMemsetAsync(h->span.p, 0, (size_t)h->P.npix_y * (h->P.npix + 1) * sizeof(unsigned long long),
                      st));
   CK(cudaMemsetAsync(h->stat.p, 0, 8 * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(h->counter.p, 0, sizeof(unsigned long long), st));
@@ -704,9 +710,9 @@ static double map_scale(const mm_map *h) {
 }
 
 static mm_status alloc_map_buffers(mm_map *h) {
-  const size_t np = (size_t)h->P.npix * h->P.npix;
+  const size_t np = (size_t)h->P.npix * h->P.npix_y;
   CK(h->acc.ensure(np));
-  CK(h->span.ensure((size_t)h->P.npix * (h->P.npix + 1)));
+  CK(h->span.ensure((size_t)h->P.npix_y * (h->P.npix + 1)));
   CK(h->map.ensure(np));
   CK(h->stat.ensure(8));
   CK(h->counter.ensure(1));
@@ -723,7 +729,7 @@ static mm_status alloc_map_buffers(mm_map *h) {
     const int64_t cells = (h->col_hi - h->col_lo) * (h->row_hi - h->row_lo);
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
-    const bool fits_l2 = 16.0 * (double)h->P.npix * (double)h->P.npix <= 0.5 * (double)l2;
+    const bool fits_l2 = 16.0 * (double)h->P.npix * (double)h->P.npix_y <= 0.5 * (double)l2;
     const int32_t want = h->mode == MM_FMM_IRS ? -1 : h->opt.big_queue_slots;
     h->bigq_cap = want < 0 ? 0
                   : want > 0 ? (int64_t)want
@@ -780,7 +786,7 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     C.hx = P.h[0];
     C.hy = P.h[1];
     C.lox = P.center_y[0] - P.half_length;
-    C.loy = P.center_y[1] - P.half_length;
+    C.loy = P.center_y[1] - P.half_length_y;
     C.delta = P.delta;
     C.rect_c1 = h->opt.star_rect[0];
     C.rect_c2 = h->opt.star_rect[1];
@@ -809,7 +815,7 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
       h->last_segments = 0;
       CKS(record(h, 5, st));
       CKS(record(h, 3, st));
-      LCH(launch_normalize(h->acc.p, h->span.p, P.npix, map_scale(h), h->map.p, st));
+      LCH(launch_normalize(h->acc.p, h->span.p, P.npix, P.npix_y, map_scale(h), h->map.p, st));
       CKS(record(h, 4, st));
       h->ev_recorded = h->opt.time_stages != 0;
       h->last_stream = st;
@@ -836,7 +842,7 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     CKS(record(h, 5, st));
   }
   CKS(record(h, 3, st));
-  LCH(launch_normalize(h->acc.p, h->span.p, P.npix, map_scale(h), h->map.p, st));
+  LCH(launch_normalize(h->acc.p, h->span.p, P.npix, P.npix_y, map_scale(h), h->map.p, st));
   CKS(record(h, 4, st));
   h->ev_recorded = h->opt.time_stages != 0;
   h->last_stream = st;
@@ -1028,7 +1034,8 @@ static std::string tune_key(int dev, const mm_options &o, int32_t fmm_order, int
   char b[256];
   snprintf(b, sizeof b, "sm_%d%d/p%d/leaf%d/sub%d/rpi%d/nstar%d/rays%d/npix%d", major, minor,
            fmm_order, leaf_size, o.sub_levels, o.rows_per_item, log2_bucket((double)n_stars),
-           log2_bucket((double)P.n[0] * (double)P.n[1]), log2_bucket((double)P.npix));
+           log2_bucket((double)P.n[0] * (double)P.n[1]),
+           log2_bucket((double)P.npix * (double)P.npix_y) / 2);
   return b;
 }
 
@@ -1284,7 +1291,7 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
     CKS(record(h, 5, st));
     LCH(launch_big_ipm(h->md, st));
     CKS(record(h, 3, st));
-    LCH(launch_normalize(h->acc.p, h->span.p, h->P.npix, map_scale(h), h->map.p, st));
+    LCH(launch_normalize(h->acc.p, h->span.p, h->P.npix, h->P.npix_y, map_scale(h), h->map.p, st));
     CKS(record(h, 4, st));
     h->ev_recorded = h->opt.time_stages != 0;
     h->last_stream = st;
@@ -1300,7 +1307,7 @@ mm_status mm_get_map(const mm_map *hc, float *out, int32_t on_device) {
   if (!h || !out) return fail(MM_EINVAL, "NULL argument");
   if (!h->ran) return fail(MM_ESTATE, "mm_run has not been called");
   CK(cudaSetDevice(h->device));
-  const size_t bytes = (size_t)h->P.npix * h->P.npix * sizeof(float);
+  const size_t bytes = (size_t)h->P.npix * h->P.npix_y * sizeof(float);
   if (on_device) {
     CK(cudaMemcpyAsync(out, h->map.p, bytes, cudaMemcpyDeviceToDevice, h->last_stream));
   } else {
@@ -1315,9 +1322,10 @@ mm_status mm_get_map_fixed(const mm_map *hc, uint64_t *out, int32_t on_device) {
   if (!h || !out) return fail(MM_EINVAL, "NULL argument");
   if (!h->ran) return fail(MM_ESTATE, "mm_run has not been called");
   CK(cudaSetDevice(h->device));
-  const size_t np = (size_t)h->P.npix * h->P.npix;
+  const size_t np = (size_t)h->P.npix * h->P.npix_y;
   CK(h->fixed_out.ensure(np));
-  LCH(launch_fold_span(h->acc.p, h->span.p, h->P.npix, h->fixed_out.p, h->last_stream));
+  LCH(launch_fold_span(h->acc.p, h->span.p, h->P.npix, h->P.npix_y, h->fixed_out.p,
+                       h->last_stream));
   if (on_device) {
     CK(cudaMemcpyAsync(out, h->fixed_out.p, np * 8, cudaMemcpyDeviceToDevice, h->last_stream));
   } else {
@@ -1358,7 +1366,7 @@ mm_status mm_shoot_points(mm_map *h, int64_t n, const double *z_xy, double *w_xy
       C.hx = P.h[0];
       C.hy = P.h[1];
       C.lox = P.center_y[0] - P.half_length;
-      C.loy = P.center_y[1] - P.half_length;
+      C.loy = P.center_y[1] - P.half_length_y;
       C.delta = P.delta;
       C.rect_c1 = h->opt.star_rect[0];
       C.rect_c2 = h->opt.star_rect[1];
@@ -1370,7 +1378,7 @@ mm_status mm_shoot_points(mm_map *h, int64_t n, const double *z_xy, double *w_xy
       }
       e = launch_probe(h->d_md.p, h->md.square_cells != 0, n, dz, dw, P.x0[0], P.x0[1], P.h[0],
                        P.h[1], h->R0, P.center_y[0] - P.half_length,
-                       P.center_y[1] - P.half_length, P.delta, h->err.p, st);
+                       P.center_y[1] - P.half_length_y, P.delta, h->err.p, st);
     }
     if (e != cudaSuccess) {
       s = fail(MM_ECUDA, "probe launch: %s", cudaGetErrorString(e));

@@ -517,8 +517,8 @@ __global__ void __launch_bounds__(64) k_leaf_finalize(TreeDev T, FmmConst C, int
     F *= 1.01;
     const double Bu = fabs(ak + C.gamma) * (Lq + hmax) / C.delta + F;
     const double Bv = fabs(ak - C.gamma) * (Lq + hmax) / C.delta + F;
-    const double Uc = U, Vc = V, n = (double)C.npix, margin = 2.0;
-    const double Dl = -(Uc + Bu), Dr = (Uc - Bu) - n, Db = -(Vc + Bv), Dt = (Vc - Bv) - n;
+    const double Uc = U, Vc = V, n = (double)C.npix, ny = (double)C.npix_y, margin = 2.0;
+    const double Dl = -(Uc + Bu), Dr = (Uc - Bu) - n, Db = -(Vc + Bv), Dt = (Vc - Bv) - ny;
     double D = Dl;
     int side = MM_CULL_LEFT;
     if (Dr > D) D = Dr, side = MM_CULL_RIGHT;

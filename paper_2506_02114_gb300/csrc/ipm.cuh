@@ -73,7 +73,7 @@ __device__ __forceinline__ unsigned long long frac_to_fixed(float f) {
 // Add v fixed-point units to map pixel (gx, gy) if it lies in the map.
 __device__ __forceinline__ void deposit(const MapDev &M, long long gx, long long gy,
                                         unsigned long long v) {
-  if (v && gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix)
+  if (v && gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix_y)
     atomicAdd(&M.acc[gy * M.npix + gx], v);
 }
 
@@ -82,7 +82,7 @@ __device__ __forceinline__ void deposit(const MapDev &M, long long gx, long long
 // copied to local memory to be addressed).
 struct MapAcc {
   unsigned long long *acc, *span;
-  int npix;
+  int npix, npix_y;
 };
 
 // Lane-private run accumulator: consecutive one-pixel triangles of a lane's
@@ -270,7 +270,7 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   // wholly beyond one edge of the map (most triangles of a shooting region):
   // integer tests on the vertices' pixels, before any arithmetic
   if (max(a.px, max(b.px, c.px)) < 0 || min(a.px, min(b.px, c.px)) >= M.npix ||
-      max(a.py, max(b.py, c.py)) < 0 || min(a.py, min(b.py, c.py)) >= M.npix)
+      max(a.py, max(b.py, c.py)) < 0 || min(a.py, min(b.py, c.py)) >= M.npix_y)
     return TRI_DONE;
   const int ox = a.px, oy = a.py;
   float t[6];
@@ -302,7 +302,8 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   if (cx0 == cx1 && cy0 == cy1) {
     // whole triangle inside one pixel
     const long long gx = (long long)ox + cx0, gy = (long long)oy + cy0;
-    if (gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix) run_add(M, ra, gy * M.npix + gx, MM_FIX_ONE);
+    if (gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix_y)
+      run_add(M, ra, gy * M.npix + gx, MM_FIX_ONE);
     return TRI_DONE;
   }
   if ((cx1 - cx0) + (cy1 - cy0) == 1) {
@@ -325,7 +326,7 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     const long long gax = b0 ? glx : glx + 1 - o, gay = b0 ? gly : gly + o;
     const long long gbx = b0 ? glx + 1 - o : glx, gby = b0 ? gly + o : gly;
     const unsigned long long va = b0 ? vlow : MM_FIX_ONE - vlow;
-    if (va && gax >= 0 && gax < M.npix && gay >= 0 && gay < M.npix)
+    if (va && gax >= 0 && gax < M.npix && gay >= 0 && gay < M.npix_y)
       run_add(M, ra, gay * M.npix + gax, va);
     deposit(M, gbx, gby, MM_FIX_ONE - va);
     cnt.line++;
@@ -333,7 +334,7 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   }
   // restrict to the map: frame columns [-ox, npix-1-ox]
   const long long mcl = -(long long)ox, mch = (long long)M.npix - 1 - ox;
-  const long long mrl = -(long long)oy, mrh = (long long)M.npix - 1 - oy;
+  const long long mrl = -(long long)oy, mrh = (long long)M.npix_y - 1 - oy;
   const long long cl = cx0 > mcl ? cx0 : mcl, ch = cx1 < mch ? cx1 : mch;
   const long long rl = cy0 > mrl ? cy0 : mrl, rh = cy1 < mrh ? cy1 : mrh;
   if (cl > ch || rl > rh) return TRI_DONE;  // misses the map
@@ -519,16 +520,17 @@ __device__ __forceinline__ void pixel_task(const MapAcc &M, const RowRecs *rr, i
 // the rows differ.  Call with all 32 lanes.
 __device__ __forceinline__ void warp_tri_jobs(unsigned long long *acc,
                                                   unsigned long long *span, int npix,
+                                                  int npix_y,
                                                   const TriJob *q, int nb, RowRecs *rr,
                                                   int lane) {
-  const MapAcc M = {acc, span, npix};
+  const MapAcc M = {acc, span, npix, npix_y};
   int rl = 0, nrows = 0;
   if (lane < nb) {
     const TriJob &J = q[lane];
     const float ymin = fminf(J.t[1], fminf(J.t[3], J.t[5]));
     const float ymax = fmaxf(J.t[1], fmaxf(J.t[3], J.t[5]));
     const int r0 = max((int)floorf(fmaxf(ymin, -1.0e9f)), -J.oy);
-    const int r1 = min((int)floorf(fminf(ymax, 1.0e9f)), M.npix - 1 - J.oy);
+    const int r1 = min((int)floorf(fminf(ymax, 1.0e9f)), M.npix_y - 1 - J.oy);
     rl = r0;
     nrows = r1 >= r0 ? r1 - r0 + 1 : 0;
   }
@@ -657,7 +659,7 @@ __device__ __forceinline__ void jq_share(const MapDev &M, JobQueue &jq, bool flu
     } else {
       if (M.bigq_cap > 0 && lane < nb && base + lane < (unsigned long long)M.bigq_cap)
         M.bigq[base + lane] = empty_job_impl();
-      warp_tri_jobs(M.acc, M.span, M.npix, jq.q + jq.n, nb, jq.rr, lane);
+      warp_tri_jobs(M.acc, M.span, M.npix, M.npix_y, jq.q + jq.n, nb, jq.rr, lane);
     }
   }
 }

@@ -105,9 +105,9 @@ struct MapDev {
   float crit_area2;           // 2 x source triangle area (px^2) below which the
                               // triangle counts as near-critical
   // map
-  int32_t npix;
-  unsigned long long *acc;    // npix*npix fixed point, 2^32 = one triangle
-  unsigned long long *span;   // npix*(npix+1) row difference array
+  int32_t npix, npix_y;       // pixels along x (row length) and y (rows)
+  unsigned long long *acc;    // npix_y*npix fixed point, 2^32 = one triangle
+  unsigned long long *span;   // npix_y*(npix+1) row difference array
   // statistics (per map)
   unsigned long long *stat;   // triangle counters, see IpmCounters
   // larger triangles handed to the second kernel (capacity 0: none)

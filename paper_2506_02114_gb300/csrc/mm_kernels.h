@@ -60,7 +60,7 @@ struct FmmConst {
   int p;                      // expansion order of the FMM
   int p_eval;                 // terms kept of each sub-cell's re-centred expansion
   int sub;                    // sub-cell levels s: 4^s sub-cells per leaf
-  int npix;                   // map pixels per side (culling bounds)
+  int npix, npix_y;           // map pixels along x and y (culling bounds)
   int cull;                   // 1: compute the culling bounds
   double kappa, gamma, kappa_star;
   double x0, y0, hx, hy;      // ray grid
@@ -99,8 +99,9 @@ cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n
                              unsigned long long *counter, unsigned *err, int grid,
                              cudaStream_t st);
 cudaError_t launch_normalize(const unsigned long long *acc, const unsigned long long *span,
-                             int npix, double scale, float *out, cudaStream_t st);
+                             int npix, int npix_y, double scale, float *out, cudaStream_t st);
 cudaError_t launch_fold_span(unsigned long long *acc, const unsigned long long *span, int npix,
+                             int npix_y,
                              unsigned long long *out, cudaStream_t st);
 cudaError_t launch_probe(const MapDev *d_maps, bool square, int64_t n, const double *z,
                          double *w, double x0, double y0, double hx, double hy, double R0,

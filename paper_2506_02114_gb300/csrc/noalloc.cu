@@ -143,6 +143,7 @@ extern "C" mm_status mm_map_plain_fp64_noalloc(
   md.col_end = n0 - 1;
   md.rows_per_item = 64;
   md.npix = npix;
+  md.npix_y = npix;  // square map
   md.acc = acc;
   md.span = span;
   md.stat = stat;
@@ -173,7 +174,7 @@ extern "C" mm_status mm_map_plain_fp64_noalloc(
       cudaSuccess)
     return fail(MM_ECUDA, "inverse polygon mapping", e);
   const double scale = std::ldexp(0.5 * C.hx * C.hy / (delta * delta), -32);
-  if ((e = launch_normalize(acc, span, npix, scale, map_out, st)) != cudaSuccess)
+  if ((e = launch_normalize(acc, span, npix, npix, scale, map_out, st)) != cudaSuccess)
     return fail(MM_ECUDA, "normalisation", e);
   return MM_OK;
 }

@@ -217,7 +217,7 @@ __device__ __forceinline__ bool cell_beyond_map(const MapDev &M, const Vtx &a, c
                                                 const Vtx &c, const Vtx &d) {
   const int x0 = min(min(a.px, b.px), min(c.px, d.px)), x1 = max(max(a.px, b.px), max(c.px, d.px));
   const int y0 = min(min(a.py, b.py), min(c.py, d.py)), y1 = max(max(a.py, b.py), max(c.py, d.py));
-  return x0 != MM_VTX_INVALID && (x1 < 0 || x0 >= M.npix || y1 < 0 || y0 >= M.npix);
+  return x0 != MM_VTX_INVALID && (x1 < 0 || x0 >= M.npix || y1 < 0 || y0 >= M.npix_y);
 }
 
 __device__ __forceinline__ Vtx shfl_down_vtx(const Vtx &v, int d) {
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
       if (owner) {
         if (v.px == MM_VTX_INVALID)
           cnt.dropped++;
-        else if (v.px >= 0 && v.px < M.npix && v.py >= 0 && v.py < M.npix)
+        else if (v.px >= 0 && v.px < M.npix && v.py >= 0 && v.py < M.npix_y)
           run_add(M, ra, (long long)v.py * M.npix + v.px, 1ull);
       }
     }
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(256, MM_BIG_MINB) k_big_ipm(const MapDev M) {
     const int nb = (int)min(32ll, n - base);
     if (lane < nb) q[w][lane] = M.bigq[base + lane];
     __syncwarp();
-    warp_tri_jobs(M.acc, M.span, M.npix, q[w], nb, &rr[w], lane);
+    warp_tri_jobs(M.acc, M.span, M.npix, M.npix_y, q[w], nb, &rr[w], lane);
   }
 }
 
@@ -497,9 +497,9 @@ __global__ void __launch_bounds__(256) k_normalize(const unsigned long long *__r
 // acc += row-prefix(span): folds the difference array into the accumulator so
 // the raw fixed-point map can be read back.
 __global__ void k_fold_span(unsigned long long *acc, const unsigned long long *span, int npix,
-                            unsigned long long *out) {
+                            int npix_y, unsigned long long *out) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= npix) return;
+  if (row >= npix_y) return;
   const unsigned long long *sp = span + (int64_t)row * (npix + 1);
   unsigned long long run = 0;
   for (int c = 0; c < npix; c++) {
@@ -593,14 +593,14 @@ cudaError_t launch_big_ipm(const MapDev &m, cudaStream_t st) {
 }
 
 cudaError_t launch_normalize(const unsigned long long *acc, const unsigned long long *span,
-                             int npix, double scale, float *out, cudaStream_t st) {
-  k_normalize<<<npix, 256, 0, st>>>(acc, span, npix, scale, out);
+                             int npix, int npix_y, double scale, float *out, cudaStream_t st) {
+  k_normalize<<<npix_y, 256, 0, st>>>(acc, span, npix, scale, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fold_span(unsigned long long *acc, const unsigned long long *span, int npix,
-                             unsigned long long *out, cudaStream_t st) {
-  k_fold_span<<<(npix + 127) / 128, 128, 0, st>>>(acc, span, npix, out);
+                             int npix_y, unsigned long long *out, cudaStream_t st) {
+  k_fold_span<<<(npix_y + 127) / 128, 128, 0, st>>>(acc, span, npix, npix_y, out);
   return cudaGetLastError();
 }
 

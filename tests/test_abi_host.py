@@ -35,11 +35,14 @@ def test_library_exports_every_declared_symbol():
     dict(kappa=1.3, gamma=0.2, s=0.9, npix=64, hl=3.0, rpp=1.0),
     dict(kappa=0.4, gamma=0.3, s=0.0, npix=256, hl=4.0, img_half=(16 / 3, 16.0),
          ray_grid=(700, 2000)),
+    dict(kappa=0.66717, gamma=0.33383, s=0.5, npix=1000, hl=50.0, rpp=1.0, npix_y=100),
+    dict(kappa=0.45, gamma=0.3, s=0.4, npix=48, hl=1.5, rpp=4.0, npix_y=80,
+         center_y=(0.4, -0.2)),
 ])
 def test_derived_parameters_match_oracle(oracle_mod, case):
     m, _ = synthetic.star_field(9, 300, 10.0, synthetic.SALPETER_01_1)
     kw = {}
-    for k in ("center_y", "img_half", "ray_grid"):
+    for k in ("center_y", "img_half", "ray_grid", "npix_y"):
         if k in case:
             kw[k] = case[k]
     got = mm.derive_params(case["kappa"], case["gamma"], case["s"], m, case["hl"], case["npix"],
@@ -48,9 +51,10 @@ def test_derived_parameters_match_oracle(oracle_mod, case):
                                    case["npix"], rays_per_pixel=case.get("rpp", 0.0),
                                    **kw).as_dict()
     for k in ("kappa_star", "a1", "a2", "mu_macro", "mean_m", "m2_over_m", "r_border",
-              "delta", "img_center", "img_half", "h", "x0"):
+              "delta", "img_center", "img_half", "h", "x0", "half_length_y"):
         np.testing.assert_allclose(got[k], ref[k], rtol=1e-14, atol=1e-14, err_msg=k)
     assert list(got["n"]) == list(ref["n"])
+    assert got["npix_y"] == ref["npix_y"] == case.get("npix_y", case["npix"])
 
 
 def test_invalid_arguments_rejected():

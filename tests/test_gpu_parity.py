@@ -436,3 +436,32 @@ def test_star_on_a_grid_vertex(oracle_mod, mode):
                      flux_fraction_f=0.01, **g)
     assert st["triangles_dropped"] == 6
     assert_map_parity(mu, mu_ref, p.mu_macro)
+
+
+@pytest.mark.parametrize("mode", [mm.MM_FMM_FP32, mm.MM_PLAIN_FP64, mm.MM_FMM_IRS])
+def test_non_square_map(oracle_mod, mode):
+    """A map of 40 x 72 square pixels (npix_y = 72) against the oracle's map
+    of the same shape: polygon mapping (FMM and plain FP64) to the map
+    tolerances, ray counts to the total within the edge rays' allowance."""
+    kappa, gamma, s, hl, npix, ny, rpp = 0.45, 0.3, 0.4, 1.0, 40, 72, 12.0
+    p0 = oracle_inputs(oracle_mod, kappa, gamma, s, np.ones(4), hl, npix, rpp,
+                       flux_fraction_f=0.01, npix_y=ny)
+    R = 1.1 * math.hypot(p0.img_half[0], p0.img_half[1])
+    n = synthetic.n_stars_for((1 - s) * kappa, R, synthetic.EQUAL)
+    m, pos = synthetic.star_field(17, n, R)
+    p = oracle_inputs(oracle_mod, kappa, gamma, s, m, hl, npix, rpp, flux_fraction_f=0.01,
+                      npix_y=ny)
+    assert p.half_length_y == 0.5 * ny * p.delta
+    mu, st = gpu_map(kappa, gamma, s, m, pos, hl, npix, fmm_order=25, mode=mode, npix_y=ny,
+                     flux_fraction_f=0.01, **explicit_grid(p))
+    assert mu.shape == (ny, npix)
+    assert st["params"]["npix_y"] == ny and st["params"]["half_length_y"] == p.half_length_y
+    if mode == mm.MM_FMM_IRS:
+        _, cnt, _ = oracle_mod.irs_map(p, m, pos)
+        mu_ref = cnt * p.h[0] * p.h[1] / p.delta ** 2
+        assert abs(mu.sum() / mu_ref.sum() - 1) < 1e-3
+        rows = mu.sum(1) / mu_ref.sum(1)            # every row of the taller map is used
+        assert np.all(np.abs(rows - 1) < 0.02), rows
+    else:
+        mu_ref, _ = oracle_mod.magnification_map(p, m, pos)
+        assert_map_parity(mu, mu_ref, p.mu_macro)
