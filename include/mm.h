@@ -282,18 +282,23 @@ mm_status mm_run(mm_map *h, void *stream);
 /*
  * Run n handles (all created in MM_FMM_FP32 mode on the current device) with
  * one persistent deflection+mapping launch whose work queue spans every map.
+ * Asynchronous like mm_run, with no host synchronisation: the batch's
+ * descriptor array is assembled on the device (hs[0] holds it), so the call
+ * can be captured in a CUDA graph once an earlier call with at least n
+ * handles led by hs[0] has sized that array.  Each map is bit-identical to
+ * its own mm_run.
  */
 mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream);
 
 /*
- * Copy the magnification map (npix*npix floats) into out.  on_device = 0:
+ * Copy the magnification map (npix_y rows of npix floats) into out.  on_device = 0:
  * out is host memory (the call synchronises); 1: out is device memory and the
  * copy is enqueued on the handle's last stream.
  */
 mm_status mm_get_map(const mm_map *h, float *out, int32_t on_device);
 
 /*
- * Copy the raw accumulator (npix*npix uint64): the sum over triangles of
+ * Copy the raw accumulator (npix_y rows of npix uint64): the sum over triangles of
  * round(fraction * 2^32) per pixel.  Integer sums make it bit-identical from
  * run to run.  Same on_device rule as mm_get_map.
  */

@@ -1259,7 +1259,8 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
   }
   CK(cudaSetDevice(hs[0]->device));
   mm_map *lead = hs[0];
-  std::vector<MapDev> mds(n);
+  std::vector<const MapDev *> src(n);
+  std::vector<int64_t> wb(n);
   int64_t work = 0;
   bool all_square = true;
   for (int i = 0; i < n; i++) {
@@ -1274,14 +1275,18 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
       CKS(prepare(h, st));
     }
     CKS(record(h, 2, st));
-    mds[i] = h->md;
-    mds[i].work_begin = work;
+    src[i] = h->d_md.p;
+    wb[i] = work;
     work += (int64_t)h->md.strips * h->md.row_blocks;
     all_square = all_square && h->md.square_cells;
   }
+  // the descriptor array is assembled on the device from the handles' own
+  // copies: no host staging and no synchronisation, so the whole batch can
+  // be captured in a CUDA graph (after one call has sized the array)
   CK(lead->batch_md.ensure(n));
-  CK(cudaMemcpyAsync(lead->batch_md.p, mds.data(), n * sizeof(MapDev), cudaMemcpyHostToDevice,
-                     st));
+  int gl = 0;
+  CK(launch_batch_gather(src.data(), wb.data(), n, lead->batch_md.p, gl, st));
+  lead->launches += gl;
   CK(launch_shoot_ipm(lead->batch_md.p, nullptr, n, work, all_square, lead->counter.p, lead->err.p,
                       shoot_grid(), st));
   lead->launches++;
@@ -1297,8 +1302,6 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
     h->last_stream = st;
     h->ran = true;
   }
-  // keep the host copy alive until the copy has been consumed
-  CK(cudaStreamSynchronize(st));
   return MM_OK;
 }
 

@@ -88,6 +88,9 @@ void build_operator_tables(int p, std::vector<double2> &MM, std::vector<double2>
 
 // ---- shooting + mapping (shoot.cu) -----------------------------------------
 // The second pass over the map's queued larger triangles (no-op without a queue).
+// dst[i] = *src[i] with work_begin[i], on the device (n descriptors)
+cudaError_t launch_batch_gather(const MapDev *const *src, const int64_t *work_begin, int n,
+                                MapDev *dst, int &launches, cudaStream_t st);
 // inverse ray shooting of one map's work items (no second pass)
 cudaError_t launch_shoot_irs(const MapDev &m, int64_t total_work, bool square,
                              unsigned long long *counter, unsigned *err, int grid,

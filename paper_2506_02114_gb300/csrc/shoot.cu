@@ -572,6 +572,44 @@ cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n
                                               grid, st);
 }
 
+// Device-side assembly of a batch's descriptor array from the handles' own
+// device copies (no host staging, so a batch can be captured in a CUDA
+// graph): block i copies map i's descriptor and sets its first work item.
+#define MM_GATHER_MAX 64
+struct BatchGather {
+  const MapDev *src[MM_GATHER_MAX];
+  int64_t work_begin[MM_GATHER_MAX];
+  int n;
+};
+static_assert(sizeof(MapDev) % 8 == 0, "MapDev copied in 8-byte words");
+
+__global__ void k_batch_gather(const BatchGather g, MapDev *dst) {
+  const int i = blockIdx.x;
+  if (i >= g.n) return;
+  const unsigned long long *s = reinterpret_cast<const unsigned long long *>(g.src[i]);
+  unsigned long long *d = reinterpret_cast<unsigned long long *>(dst + i);
+  for (int k = threadIdx.x; k < (int)(sizeof(MapDev) / 8); k += blockDim.x) d[k] = s[k];
+  __syncthreads();
+  if (threadIdx.x == 0) dst[i].work_begin = g.work_begin[i];
+}
+
+cudaError_t launch_batch_gather(const MapDev *const *src, const int64_t *work_begin, int n,
+                                MapDev *dst, int &launches, cudaStream_t st) {
+  for (int b = 0; b < n; b += MM_GATHER_MAX) {
+    BatchGather g;
+    g.n = min(MM_GATHER_MAX, n - b);
+    for (int k = 0; k < g.n; k++) {
+      g.src[k] = src[b + k];
+      g.work_begin[k] = work_begin[b + k];
+    }
+    k_batch_gather<<<g.n, 64, 0, st>>>(g, dst + b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    launches++;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_shoot_irs(const MapDev &m, int64_t total_work, bool square,
                              unsigned long long *counter, unsigned *err, int grid,
                              cudaStream_t st) {

@@ -41,6 +41,12 @@ def batch_maps(oracle_mod, n_maps, seed=7):
         if n < 20 or n > 20000:
             continue
         m, pos = synthetic.star_field(d["seed"], n, R, synthetic.SALPETER_01_1)
+        # few stars may not reach the shooting region's corners: skip those
+        p = oracle_mod.derive_params(kappa, gamma, s, m, hl, npix, rays_per_pixel=rpp,
+                                     flux_fraction_f=0.01)
+        if any(pos[:, k].min() > p.x0[k] or pos[:, k].max() < p.x0[k] + (p.n[k] - 1) * p.h[k]
+               for k in (0, 1)):
+            continue
         out.append(dict(kappa=kappa, gamma=gamma, s=s, npix=npix, hl=hl, rpp=rpp, m=m, pos=pos))
         if len(out) == n_maps:
             return out
@@ -120,3 +126,40 @@ def test_full_size_workload_tiles(oracle_mod, torch_cuda, name):
     assert (mu_ref > 0).sum() > 10
     e = band_errors(mu, mu_ref, p.mu_macro)
     assert e["p999"] <= MAP_P999_TOL and e["mean_rel"] <= MEAN_TOL, e
+
+
+def test_sweep_of_128_maps_autotuned_in_one_graph(oracle_mod, torch_cuda, tmp_path):
+    """The batched sweep's shape: 128 maps of uneven sizes and (kappa, gamma,
+    s), each autotuned (one shared cache), run as one batch captured in a
+    CUDA graph.  The replay reproduces the eager batch bit for bit, single
+    runs equal it, and the cheapest map meets the oracle."""
+    torch = torch_cuda
+    maps = batch_maps(oracle_mod, 128, seed=21)
+    assert len(maps) == 128
+    cache = str(tmp_path / "tune.jsonl")
+    hs = [make(w, autotune=True, tune_cache=cache) for w in maps]
+    assert {mm.get_stats(h)["autotuned"] for h in hs} <= {1, 2}
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        mm.run_batch(hs, s.cuda_stream)
+    s.synchronize()
+    eager = [mm.get_map_fixed(h) for h in hs]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        mm.run_batch(hs, s.cuda_stream)
+    g.replay()
+    torch.cuda.synchronize()
+    for h, e in zip(hs, eager):
+        assert np.array_equal(mm.get_map_fixed(h), e)
+    for k in (0, 63, 127):
+        mm.run(hs[k], 0)
+        assert np.array_equal(mm.get_map_fixed(hs[k]), eager[k])
+    k = min(range(len(maps)), key=lambda i: mm.get_stats(hs[i])["rays"] * len(maps[i]["m"]))
+    mu = mm.get_map(hs[k])
+    for h in hs:
+        mm.destroy(h)
+    w = maps[k]
+    p = oracle_mod.derive_params(w["kappa"], w["gamma"], w["s"], w["m"], w["hl"], w["npix"],
+                                 rays_per_pixel=w["rpp"], flux_fraction_f=0.01)
+    mu_ref, _ = oracle_mod.magnification_map(p, w["m"], w["pos"])
+    assert_map_parity(mu, mu_ref, p.mu_macro)
