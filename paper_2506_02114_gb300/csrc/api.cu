@@ -810,8 +810,7 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     const int64_t work =
         (int64_t)h->md.strips * ((h->md.row_blocks + h->md.item_stride - 1) / h->md.item_stride);
     if (h->mode == MM_FMM_IRS) {
-      LCH(launch_shoot_irs(h->md, work, h->md.square_cells != 0, h->counter.p, h->err.p,
-                          shoot_grid(), st));
+      LCH(launch_shoot_irs(h->md, work, h->md.square_cells != 0, h->counter.p, h->err.p, st));
       h->last_segments = 0;
       CKS(record(h, 5, st));
       CKS(record(h, 3, st));

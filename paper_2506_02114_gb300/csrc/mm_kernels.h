@@ -93,8 +93,7 @@ cudaError_t launch_batch_gather(const MapDev *const *src, const int64_t *work_be
                                 MapDev *dst, int &launches, cudaStream_t st);
 // inverse ray shooting of one map's work items (no second pass)
 cudaError_t launch_shoot_irs(const MapDev &m, int64_t total_work, bool square,
-                             unsigned long long *counter, unsigned *err, int grid,
-                             cudaStream_t st);
+                             unsigned long long *counter, unsigned *err, cudaStream_t st);
 cudaError_t launch_big_ipm(const MapDev &m, cudaStream_t st);
 // h_single: the map by value when n_maps == 1 (else NULL: maps from d_maps)
 cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n_maps,
