@@ -465,3 +465,16 @@ def test_non_square_map(oracle_mod, mode):
     else:
         mu_ref, _ = oracle_mod.magnification_map(p, m, pos)
         assert_map_parity(mu, mu_ref, p.mu_macro)
+
+
+def test_oversized_map_fails_with_enomem(oracle_mod):
+    """A map whose accumulators exceed device memory (200 000^2 pixels, 640 GB)
+    fails with MM_ENOMEM, allocating nothing it keeps; the GPU stays usable
+    and the next handle works."""
+    with pytest.raises(mm.MMError) as e:
+        mm.create(0.4, 0.3, 1.0, [], np.zeros((0, 2)), 1.0, 200000, img_half=(2.0, 2.0),
+                  ray_grid=(64, 64))
+    assert e.value.status == mm.MM_ENOMEM
+    mu, st = gpu_map(0.4, 0.3, 1.0, [], np.zeros((0, 2)), 1.0, 16, img_half=(2.0, 5.0),
+                     ray_grid=(64, 160))
+    assert st["triangles_dropped"] == 0 and mu.max() > 0
