@@ -21,9 +21,11 @@
  *     mm_last_error() returns a thread-local message for the last failure.
  *   - Positions are interleaved (x, y) doubles; units are Einstein radii of a
  *     unit mass (theta_star = 1).
- *   - A map is npix*npix values, row-major, row index = y pixel; pixel (px, py)
- *     covers [c_x - L + px*d, c_x - L + (px+1)*d) x (same in y), with
- *     L = half_length, d = 2L/npix, c = map centre.
+ *   - A map is npix_y rows of npix values (npix_y = npix unless
+ *     mm_options.npix_y is set), row-major, row index = y pixel; pixel
+ *     (px, py) covers [c_x - L + px*d, c_x - L + (px+1)*d) x
+ *     [c_y - L_y + py*d, c_y - L_y + (py+1)*d), with L = half_length,
+ *     d = 2L/npix, L_y = npix_y d / 2 and c the map centre.
  *   - A handle owns all of its device memory and is used by one host thread
  *     at a time.  Different handles may run concurrently on different streams.
  *     Its buffers come from the device's default memory pool (stream-ordered
@@ -334,7 +336,8 @@ mm_status mm_get_stats(const mm_map *h, mm_stats *out);
  *   ray_grid[2] (host): rays per axis; grid_origin[2], grid_spacing[2]
  *     (host): image-plane position of vertex (0, 0) and the ray spacings,
  *     e.g. mm_params.n, .x0 and .h of an equivalent handle.
- *   map_out: DEVICE pointer, npix*npix floats, row-major, row = y.
+ *   map_out: DEVICE pointer, npix*npix floats, row-major, row = y (square
+ *     maps only).
  *
  * Scratch lives in one fixed device array inside the library (about 9.5 MB,
  * held by every GPU that loads it until the process exits), so sizes are

@@ -121,7 +121,7 @@ int or_map_from_vertices(const or_params *p, const double *w_xy,
 
 /* Inverse ray shooting over the vertices of rows [row_begin, row_end] and
  * columns [col_begin, col_end] (both inclusive; row_end < 0 or col_end < 0
- * means up to the grid's last vertex): counts (npix*npix, may be NULL) gets
+ * means up to the grid's last vertex): counts (npix_y rows of npix, may be NULL) gets
  * the rays per pixel, mu_out (may be NULL) count * h_x h_y / delta^2, and
  * *dropped the rays with a non-finite source position.  Pixel (px, py)
  * holds the rays with floor((w - (center - half_length)) / delta) = (px, py).
