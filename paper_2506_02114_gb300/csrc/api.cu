@@ -17,6 +17,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -359,6 +361,23 @@ static T read_scalar(const T *dptr, cudaStream_t st, cudaError_t &e) {
   return v;
 }
 
+// Host operator tables of order p (App. C.2), built once per process and
+// shared by every handle of that order.
+struct OpTables {
+  std::vector<double2> MM, ML, LL;
+};
+static const OpTables &operator_tables(int p) {
+  static std::mutex mu;
+  static std::map<int, std::unique_ptr<OpTables>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  std::unique_ptr<OpTables> &t = cache[p];
+  if (!t) {
+    t.reset(new OpTables);
+    build_operator_tables(p, t->MM, t->ML, t->LL);
+  }
+  return *t;
+}
+
 // Morton sort + levels.  plan: learn and store the level counts (host reads).
 static mm_status run_tree(mm_map *h, cudaStream_t st, bool plan) {
   const int64_t N = h->N;
@@ -513,8 +532,8 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
       h->p = std::min(MM_PMAX, std::max(2, p));
     }
     h->p_eval = eval_terms(h->p, h->sub);
-    std::vector<double2> MMh, MLh, LLh;
-    build_operator_tables(h->p, MMh, MLh, LLh);
+    const OpTables &ops = operator_tables(h->p);
+    const std::vector<double2> &MMh = ops.MM, &MLh = ops.ML, &LLh = ops.LL;
     CK(h->MMop.ensure(MMh.size()));
     CK(h->MLop.ensure(MLh.size()));
     CK(h->LLop.ensure(LLh.size()));
@@ -523,8 +542,7 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
     CK(cudaMemcpyAsync(h->MLop.p, MLh.data(), MLh.size() * sizeof(double2),
                        cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(h->LLop.p, LLh.data(), LLh.size() * sizeof(double2),
-                       cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
+                       cudaMemcpyHostToDevice, st));  // (the cached tables outlive the copies)
     CK(h->mp.ensure((size_t)nn * (h->p + 1)));
     CK(h->loc.ensure((size_t)nn * (h->p + 1)));
     CK(h->near_cnt.ensure(h->n_active << (2 * h->sub)));
@@ -590,15 +608,17 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
 
   if (plan) {
     // lookup grid over the active cell rectangle, as deep as 4M entries allow
-    cudaError_t e;
-    int CX0 = read_scalar(h->col_cell.p + h->col_lo, st, e);
-    CK(e);
-    int CX1 = read_scalar(h->col_cell.p + h->col_hi, st, e);
-    CK(e);
-    int CY0 = read_scalar(h->row_cell.p + h->row_lo, st, e);
-    CK(e);
-    int CY1 = read_scalar(h->row_cell.p + h->row_hi, st, e);
-    CK(e);
+    int cr[4] = {0, 0, 0, 0};  // one synchronisation for the four corners
+    CK(cudaMemcpyAsync(&cr[0], h->col_cell.p + h->col_lo, sizeof(int), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaMemcpyAsync(&cr[1], h->col_cell.p + h->col_hi, sizeof(int), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaMemcpyAsync(&cr[2], h->row_cell.p + h->row_lo, sizeof(int), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaMemcpyAsync(&cr[3], h->row_cell.p + h->row_hi, sizeof(int), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    const int CX0 = cr[0], CX1 = cr[1], CY0 = cr[2], CY1 = cr[3];
     // (deep enough to resolve sub-cells where entries allow)
     int gl = std::min(MM_DMAX, h->max_leaf_level + h->sub);
     for (; gl > 0; gl--) {
