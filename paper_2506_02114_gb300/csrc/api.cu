@@ -241,6 +241,11 @@ struct mm_map {
   // its second (time_stages only).
   int64_t segments = 1, last_segments = 0;
   std::vector<cudaEvent_t> seg_ev;
+
+  // pinned host scratch for the plan's small reads and uploads: [0, 4) read
+  // slots, [8, 8 + MM_DMAX + 2) the level offsets (pageable copies of a few
+  // bytes would each wait for the stream)
+  int64_t *pin = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -353,14 +358,6 @@ static mm_status cub_call(mm_map *h, bool plan, F &&f) {
   return MM_OK;
 }
 
-template <class T>
-static T read_scalar(const T *dptr, cudaStream_t st, cudaError_t &e) {
-  T v{};
-  e = cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return v;
-}
-
 // Host operator tables of order p (App. C.2), built once per process and
 // shared by every handle of that order.
 struct OpTables {
@@ -376,6 +373,28 @@ static const OpTables &operator_tables(int p) {
     build_operator_tables(p, t->MM, t->ML, t->LL);
   }
   return *t;
+}
+
+// Reads n (<= 4) int32 device values through the pinned scratch: the copies
+// are enqueued together and one synchronisation waits for all of them.
+static mm_status read_ints(mm_map *h, cudaStream_t st, int n, const int32_t *const *src,
+                           int32_t *out) {
+  int32_t *slot = reinterpret_cast<int32_t *>(h->pin);
+  for (int k = 0; k < n; k++)
+    CK(cudaMemcpyAsync(slot + k, src[k], sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int k = 0; k < n; k++) out[k] = slot[k];
+  return MM_OK;
+}
+
+// Uploads the host level offsets through the pinned scratch (the caller's
+// next read_ints completes the copy before the scratch is rewritten).
+static mm_status upload_level_off(mm_map *h, cudaStream_t st) {
+  int64_t *lo = h->pin + 8;
+  for (int k = 0; k < MM_DMAX + 2; k++) lo[k] = h->level_off[k];
+  CK(cudaMemcpyAsync(h->d_level_off.p, lo, (MM_DMAX + 2) * sizeof(int64_t),
+                     cudaMemcpyHostToDevice, st));
+  return MM_OK;
 }
 
 // Morton sort + levels.  plan: learn and store the level counts (host reads).
@@ -406,8 +425,8 @@ static mm_status run_tree(mm_map *h, cudaStream_t st, bool plan) {
     h->level_cnt[0] = 1;
     h->level_off[1] = 1;
     CK(h->d_level_off.ensure(MM_DMAX + 2));
-    CK(cudaMemcpyAsync(h->d_level_off.p, h->level_off.data(), (MM_DMAX + 2) * sizeof(int64_t),
-                       cudaMemcpyHostToDevice, st));
+    if (!h->pin) CK(cudaMallocHost(&h->pin, (8 + MM_DMAX + 2) * sizeof(int64_t)));
+    CKS(upload_level_off(h, st));
     CK(h->code.ensure(5, true));
     CK(h->lvl.ensure(5, true));
     CK(h->sbeg.ensure(5, true));
@@ -427,12 +446,10 @@ static mm_status run_tree(mm_map *h, cudaStream_t st, bool plan) {
       return cub::DeviceScan::ExclusiveSum(tmp, bytes, h->split.p, h->scan.p, (int)n, st);
     }));
     if (plan) {
-      cudaError_t e;
-      int32_t a = read_scalar(h->scan.p + (n - 1), st, e);
-      CK(e);
-      int32_t b = read_scalar(h->split.p + (n - 1), st, e);
-      CK(e);
-      const int64_t nxt = 4 * (int64_t)(a + b);
+      const int32_t *src[2] = {h->scan.p + (n - 1), h->split.p + (n - 1)};
+      int32_t ab[2];
+      CKS(read_ints(h, st, 2, src, ab));
+      const int64_t nxt = 4 * (int64_t)(ab[0] + ab[1]);
       h->level_cnt[l + 1] = nxt;
       h->level_off[l + 1] = h->level_off[l] + n;
       if (l + 2 <= MM_DMAX + 1) h->level_off[l + 2] = h->level_off[l + 1] + nxt;
@@ -442,8 +459,7 @@ static mm_status run_tree(mm_map *h, cudaStream_t st, bool plan) {
       CK(h->sbeg.ensure(need, true));
       CK(h->send.ensure(need, true));
       CK(h->first_child.ensure(need, true));
-      CK(cudaMemcpyAsync(h->d_level_off.p, h->level_off.data(), (MM_DMAX + 2) * sizeof(int64_t),
-                         cudaMemcpyHostToDevice, st));
+      CKS(upload_level_off(h, st));
       T = tree_dev(h);
     }
     LCH(launch_level_children(T, l, n, h->split.p, h->scan.p, h->code.p, h->lvl.p, h->sbeg.p,
@@ -498,12 +514,10 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
     return cub::DeviceScan::ExclusiveSum(tmp, bytes, h->leaf_flag.p, h->leaf_scan.p, (int)nn, st);
   }));
   if (plan) {
-    cudaError_t e;
-    int32_t a = read_scalar(h->leaf_scan.p + (nn - 1), st, e);
-    CK(e);
-    int32_t b = read_scalar(h->leaf_flag.p + (nn - 1), st, e);
-    CK(e);
-    h->n_active = (int64_t)a + b;
+    const int32_t *src[2] = {h->leaf_scan.p + (nn - 1), h->leaf_flag.p + (nn - 1)};
+    int32_t ab[2];
+    CKS(read_ints(h, st, 2, src, ab));
+    h->n_active = (int64_t)ab[0] + ab[1];
     if (h->n_active <= 0) return fail(MM_ECUDA, "internal: no active leaf");
     CK(h->active_list.ensure(h->n_active));
   }
@@ -591,12 +605,10 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
                                          st);
   }));
   if (plan) {
-    cudaError_t e;
-    int32_t a = read_scalar(h->near_off.p + (n_rec - 1), st, e);
-    CK(e);
-    int32_t b = read_scalar(h->near_cnt.p + (n_rec - 1), st, e);
-    CK(e);
-    h->n_near = (int64_t)a + b;
+    const int32_t *src[2] = {h->near_off.p + (n_rec - 1), h->near_cnt.p + (n_rec - 1)};
+    int32_t ab[2];
+    CKS(read_ints(h, st, 2, src, ab));
+    h->n_near = (int64_t)ab[0] + ab[1];
     CK(h->leaf.ensure(n_rec));
     CK(h->near_pos.ensure(h->n_near));
     CK(h->near_m.ensure(h->n_near));
@@ -608,16 +620,10 @@ static mm_status run_fmm(mm_map *h, cudaStream_t st, bool plan) {
 
   if (plan) {
     // lookup grid over the active cell rectangle, as deep as 4M entries allow
-    int cr[4] = {0, 0, 0, 0};  // one synchronisation for the four corners
-    CK(cudaMemcpyAsync(&cr[0], h->col_cell.p + h->col_lo, sizeof(int), cudaMemcpyDeviceToHost,
-                       st));
-    CK(cudaMemcpyAsync(&cr[1], h->col_cell.p + h->col_hi, sizeof(int), cudaMemcpyDeviceToHost,
-                       st));
-    CK(cudaMemcpyAsync(&cr[2], h->row_cell.p + h->row_lo, sizeof(int), cudaMemcpyDeviceToHost,
-                       st));
-    CK(cudaMemcpyAsync(&cr[3], h->row_cell.p + h->row_hi, sizeof(int), cudaMemcpyDeviceToHost,
-                       st));
-    CK(cudaStreamSynchronize(st));
+    const int32_t *src[4] = {h->col_cell.p + h->col_lo, h->col_cell.p + h->col_hi,
+                             h->row_cell.p + h->row_lo, h->row_cell.p + h->row_hi};
+    int32_t cr[4];
+    CKS(read_ints(h, st, 4, src, cr));
     const int CX0 = cr[0], CX1 = cr[1], CY0 = cr[2], CY1 = cr[3];
     // (deep enough to resolve sub-cells where entries allow)
     int gl = std::min(MM_DMAX, h->max_leaf_level + h->sub);
@@ -1554,6 +1560,7 @@ void mm_destroy(mm_map *h) {
     cudaStreamSynchronize(h->plan_stream);
     cudaStreamDestroy(h->plan_stream);
   }
+  if (h->pin) cudaFreeHost(h->pin);
   delete h;
 }
 
