@@ -74,6 +74,9 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
   const int maxcnt = __reduce_max_sync(0xffffffffu, near_cnt);
   const float4 *np_ = reinterpret_cast<const float4 *>(M.near_pos) + near_off;
   const float *nm_ = M.near_m + near_off;
+  // a lane with fewer stars than the warp's most runs stand-ins whose
+  // contribution is selected away after the reciprocal (a stand-in on a
+  // vertex would otherwise give 0 x 1/0 = NaN there)
   int k = 0;
   for (; k + 1 < maxcnt; k += 2) {
     const bool a0 = k < near_cnt, a1 = k + 1 < near_cnt;
@@ -90,7 +93,7 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
     }
     const float r0 = SQUARE ? fmaf(dx0, dx0, dy0 * dy0) : fmaf(dx0, dx0, M.rho * dy0 * dy0);
     const float r1 = SQUARE ? fmaf(dx1, dx1, dy1 * dy1) : fmaf(dx1, dx1, M.rho * dy1 * dy1);
-    const float q0 = m0 * rcp_approx(r0), q1 = m1 * rcp_approx(r1);
+    const float q0 = a0 ? m0 * rcp_approx(r0) : 0.f, q1 = a1 ? m1 * rcp_approx(r1) : 0.f;
     Sx = fmaf(q0, dx0, Sx);
     Sy = fmaf(q0, dy0, Sy);
     Sx2 = fmaf(q1, dx1, Sx2);

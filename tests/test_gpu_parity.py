@@ -478,3 +478,47 @@ def test_oversized_map_fails_with_enomem(oracle_mod):
     mu, st = gpu_map(0.4, 0.3, 1.0, [], np.zeros((0, 2)), 1.0, 16, img_half=(2.0, 5.0),
                      ray_grid=(64, 160))
     assert st["triangles_dropped"] == 0 and mu.max() > 0
+
+
+def test_irs_and_ipm_agree_at_full_size():
+    """The paper's consistency check of the two mapping methods (Sec. 3.2,
+    Table 1) on the benchmark workload at full size (1.475e9 rays): the ray
+    counts per 40 x 40-pixel block (4e4 to 2e5 rays each) match the polygon
+    mapping's expected counts within the counting noise, and the maps' means
+    agree much better still."""
+    wl = synthetic.workload("fmm_fp32_salpeter_2000")
+    m, pos = wl.stars()
+    args = (wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, wl.npix, wl.rays_per_pixel)
+    maps = {}
+    for mode in (mm.MM_FMM_FP32, mm.MM_FMM_IRS):
+        h = mm.create(*args, fmm_order=wl.fmm_order, mode=mode)
+        mm.run(h, 0)
+        maps[mode] = mm.get_map(h).astype(np.float64)
+        st = mm.get_stats(h)
+        mm.destroy(h)
+    per_ray = st["params"]["delta"] ** 2 / (st["params"]["h"][0] * st["params"]["h"][1])
+    b = 40
+    blk = lambda a: a.reshape(wl.npix // b, b, wl.npix // b, b).sum(axis=(1, 3)) * per_ray
+    irs, ipm = blk(maps[mm.MM_FMM_IRS]), blk(maps[mm.MM_FMM_FP32])  # rays per block
+    assert irs.min() > 2e4
+    z = (irs - ipm) / np.sqrt(ipm)
+    assert np.abs(z).max() < 6.0, np.abs(z).max()
+    assert abs(irs.sum() / ipm.sum() - 1) < 2.0 / math.sqrt(ipm.sum())
+
+
+def test_lanes_with_fewer_direct_stars(oracle_mod):
+    """A field whose warps mix sub-cells with different numbers of direct
+    stars (255 stars, 48^2 map, 715 x 2426 rays, p = 20).  A lane with fewer
+    stars than the warp's most evaluates massless stand-ins; none may land on
+    a vertex, so no triangle is dropped and the map meets the tolerances."""
+    kappa, gamma, s, hl, npix, rpp, f = 0.45, 0.3, 0.4, 1.5, 48, 8.0, 0.01
+    p0 = oracle_inputs(oracle_mod, kappa, gamma, s, np.ones(4), hl, npix, rpp, flux_fraction_f=f)
+    R = 1.1 * math.hypot(p0.img_half[0], p0.img_half[1])
+    m, pos = synthetic.star_field(5, synthetic.n_stars_for((1 - s) * kappa, R, synthetic.EQUAL), R)
+    p = oracle_inputs(oracle_mod, kappa, gamma, s, m, hl, npix, rpp, flux_fraction_f=f)
+    mu_ref, st_ref = oracle_mod.magnification_map(p, m, pos)
+    for sub in (1, 2):
+        mu, st = gpu_map(kappa, gamma, s, m, pos, hl, npix, fmm_order=20, sub_levels=sub,
+                         **explicit_grid(p))
+        assert st["triangles_dropped"] == st_ref["dropped"] == 0, sub
+        assert_map_parity(mu, mu_ref, p.mu_macro)
