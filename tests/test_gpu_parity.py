@@ -522,3 +522,48 @@ def test_lanes_with_fewer_direct_stars(oracle_mod):
                          **explicit_grid(p))
         assert st["triangles_dropped"] == st_ref["dropped"] == 0, sub
         assert_map_parity(mu, mu_ref, p.mu_macro)
+
+
+def _random_field(oracle_mod, k):
+    """Field k of a seeded family of small maps: kappa, gamma, s, size, rays
+    per pixel and mass function drawn per field (the oracle's map in seconds);
+    draws whose few stars do not span the ray grid are redrawn."""
+    for t in range(50):
+        f = _random_field_draw(oracle_mod, 100 * k + t)
+        _, m, pos, p = f
+        if all(pos[:, a].min() <= p.x0[a] and pos[:, a].max() >= p.x0[a] + (p.n[a] - 1) * p.h[a]
+               for a in (0, 1)):
+            return f
+    raise AssertionError("no covered draw")
+
+
+def _random_field_draw(oracle_mod, k):
+    u = synthetic.uniform(7000 + k, 0, 6)
+    kappa, gamma = 0.2 + 0.6 * u[0], 0.1 + 0.5 * u[1]
+    if abs(abs(1 - kappa) - gamma) < 0.08:
+        gamma = abs(1 - kappa) + 0.1
+    s = (0.0, 0.3, 0.6)[int(u[2] * 3)]
+    npix = 24 + int(u[3] * 40)
+    hl = 0.8 + 1.2 * u[4]
+    rpp = 100.0 * abs((1 - kappa) ** 2 - gamma ** 2) / 8.0
+    mass_fn = synthetic.SALPETER_01_1 if u[5] < 0.5 else synthetic.EQUAL
+    p0 = oracle_inputs(oracle_mod, kappa, gamma, s, np.ones(4), hl, npix, rpp, flux_fraction_f=0.01)
+    R = 1.1 * math.hypot(p0.img_half[0], p0.img_half[1])
+    m, pos = synthetic.star_field(7100 + k, synthetic.n_stars_for((1 - s) * kappa, R, mass_fn), R,
+                                  mass_fn)
+    p = oracle_inputs(oracle_mod, kappa, gamma, s, m, hl, npix, rpp, flux_fraction_f=0.01)
+    return (kappa, gamma, s, hl, npix), m, pos, p
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_random_small_fields(oracle_mod, k):
+    """Eight seeded random fields, each with whole leaves and with one and two
+    sub-cell levels: the dropped-triangle count equals the oracle's and the
+    map meets the tolerances."""
+    (kappa, gamma, s, hl, npix), m, pos, p = _random_field(oracle_mod, k)
+    mu_ref, st_ref = oracle_mod.magnification_map(p, m, pos)
+    for sub in (-1, 1, 2):
+        mu, st = gpu_map(kappa, gamma, s, m, pos, hl, npix, fmm_order=25, sub_levels=sub,
+                         **explicit_grid(p))
+        assert st["triangles_dropped"] == st_ref["dropped"], (sub, st["triangles_dropped"])
+        assert_map_parity(mu, mu_ref, p.mu_macro)
