@@ -163,12 +163,25 @@ __global__ void k_local(TreeDev T, int level, int64_t n, int p, const int32_t *n
         for (int c = 0; c < 4; c++) {
           const int ox = 2 * qx + (c & 1) - nx, oy = 2 * qy + (c >> 1) - ny;
           if (abs(ox) <= 1 && abs(oy) <= 1) continue;  // neighbour: near field
-          for (int k = threadIdx.x; k < P1; k += blockDim.x)
-            src[k] = mp[(int64_t)(fc + c) * P1 + k];
+          // factored M2L: b_k = (-1/z0)^k a_k, then
+          // c_l += (1/z0)^l (-a_0 / l + sum_k C(l+k-1, k-1) b_k)
+          const double2 *pw =
+              MLop + (int64_t)P1 * P1 + (int64_t)((oy + 3) * 7 + (ox + 3)) * 2 * P1;
+          for (int k = threadIdx.x; k < P1; k += blockDim.x) {
+            const double2 a = mp[(int64_t)(fc + c) * P1 + k];
+            src[k] = k ? cfma(pw[k], a, make_double2(0.0, 0.0)) : a;
+          }
           __syncthreads();
-          const double2 *op = MLop + (int64_t)((oy + 3) * 7 + (ox + 3)) * P1 * P1;
-          if (on)
-            for (int k = 0; k <= p; k++) acc = cfma(op[k * P1 + l], src[k], acc);
+          if (on) {
+            const double2 *bl = MLop + (int64_t)l * P1;  // binomials of row l, 1/l at k = 0
+            double tx = -src[0].x * bl[0].x, ty = -src[0].y * bl[0].x;
+            for (int k = 1; k <= p; k++) {
+              const double b = bl[k].x;
+              tx = fma(b, src[k].x, tx);
+              ty = fma(b, src[k].y, ty);
+            }
+            acc = cfma(pw[P1 + l], make_double2(tx, ty), acc);
+          }
           __syncthreads();
         }
       } else {
@@ -595,22 +608,28 @@ void build_operator_tables(int p, std::vector<double2> &MM, std::vector<double2>
       }
     }
   }
-  // M2L: source centre relative to the target, z0 = 2 (dx + i dy)
+  // M2L: source centre relative to the target, z0 = 2 (dx + i dy).  The
+  // operator factors as op[k][l] = (1/z0)^l C(l+k-1, k-1) (-1/z0)^k for
+  // k >= 1 and op[0][l] = -(1/z0)^l / l, so the table holds the real
+  // binomials once ([l][k], with 1/l in the unused k = 0 slot) and, per
+  // offset, the powers of -1/z0 (scaling the multipoles) and of 1/z0
+  // (scaling the sums): P1^2 + 49 x 2 P1 entries.
+  ML.assign((size_t)P1 * P1 + (size_t)49 * 2 * P1, make_double2(0.0, 0.0));
+  for (int l = 1; l <= p; l++) {
+    ML[(size_t)l * P1].x = 1.0 / l;
+    for (int k = 1; k <= p; k++) ML[(size_t)l * P1 + k].x = C[l + k - 1][k - 1];
+  }
   for (int dy = -3; dy <= 3; dy++)
     for (int dx = -3; dx <= 3; dx++) {
       if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
       cplx z0{2.0 * dx, 2.0 * dy};
       cplx iz = cinv(z0);
       cplx imz = cinv(cplx{-z0.x, -z0.y});
-      double2 *op = &ML[(size_t)((dy + 3) * 7 + (dx + 3)) * P1 * P1];
-      for (int l = 1; l <= p; l++) {
-        cplx izl = cpw(iz, l);
-        op[0 * P1 + l] = make_double2(-izl.x / l, -izl.y / l);
-        for (int k = 1; k <= p; k++) {
-          cplx t = cm(izl, cpw(imz, k));
-          double b = C[l + k - 1][k - 1];
-          op[k * P1 + l] = make_double2(t.x * b, t.y * b);
-        }
+      double2 *pw = &ML[(size_t)P1 * P1 + (size_t)((dy + 3) * 7 + (dx + 3)) * 2 * P1];
+      for (int k = 0; k <= p; k++) {
+        const cplx a = cpw(imz, k), b = cpw(iz, k);
+        pw[k] = make_double2(a.x, a.y);
+        pw[P1 + k] = make_double2(b.x, b.y);
       }
     }
 }
