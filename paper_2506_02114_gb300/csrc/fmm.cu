@@ -99,15 +99,30 @@ __global__ void k_m2m(TreeDev T, int level, int64_t n, int p, const double2 *__r
   if (fc < 0) return;
   __shared__ double2 a[4][MM_PMAX + 1];
   const int P1 = p + 1;
-  for (int idx = threadIdx.x; idx < 4 * P1; idx += blockDim.x)
-    a[idx / P1][idx % P1] = mp[(int64_t)(fc + idx / P1) * P1 + idx % P1];
+  // factored M2M: b_k = z0^-k a_k per child, then
+  // c_l = sum_q (z0/2)^l (-a_0 / l + sum_{k<=l} C(l-1, k-1) b_k), c_0 = sum_q a_0
+  for (int idx = threadIdx.x; idx < 4 * P1; idx += blockDim.x) {
+    const int q = idx / P1, k = idx % P1;
+    const double2 v = mp[(int64_t)(fc + q) * P1 + k];
+    a[q][k] = k ? cfma(MMop[(int64_t)P1 * P1 + q * 2 * P1 + k], v, make_double2(0.0, 0.0)) : v;
+  }
   __syncthreads();
   const int l = threadIdx.x;
   if (l > p) return;
   double2 s = make_double2(0.0, 0.0);
-  for (int q = 0; q < 4; q++) {
-    const double2 *op = MMop + (int64_t)q * P1 * P1;
-    for (int k = 0; k <= l; k++) s = cfma(op[k * P1 + l], a[q][k], s);
+  if (l == 0) {
+    for (int q = 0; q < 4; q++) s = make_double2(s.x + a[q][0].x, s.y + a[q][0].y);
+  } else {
+    const double2 *bl = MMop + (int64_t)l * P1;  // binomials of row l, 1/l at k = 0
+    for (int q = 0; q < 4; q++) {
+      double tx = -a[q][0].x * bl[0].x, ty = -a[q][0].y * bl[0].x;
+      for (int k = 1; k <= l; k++) {
+        const double b = bl[k].x;
+        tx = fma(b, a[q][k].x, tx);
+        ty = fma(b, a[q][k].y, ty);
+      }
+      s = cfma(MMop[(int64_t)P1 * P1 + q * 2 * P1 + P1 + l], make_double2(tx, ty), s);
+    }
   }
   mp[node * P1 + l] = s;
 }
@@ -578,23 +593,25 @@ void build_operator_tables(int p, std::vector<double2> &MM, std::vector<double2>
                            std::vector<double2> &LL) {
   const int P1 = p + 1;
   auto C = binomials(2 * p + 1);
-  MM.assign((size_t)4 * P1 * P1, make_double2(0.0, 0.0));
+  // M2M factored like M2L below: op[k][l] = (z0/2)^l C(l-1, k-1) z0^-k for
+  // 1 <= k <= l and op[0][l] = -(z0/2)^l / l: the real binomials ([l][k],
+  // 1/l at k = 0), then per child quadrant the powers z0^-k and (z0/2)^l
+  MM.assign((size_t)P1 * P1 + (size_t)4 * 2 * P1, make_double2(0.0, 0.0));
+  for (int l = 1; l <= p; l++) {
+    MM[(size_t)l * P1].x = 1.0 / l;
+    for (int k = 1; k <= l; k++) MM[(size_t)l * P1 + k].x = C[l - 1][k - 1];
+  }
   LL.assign((size_t)4 * P1 * P1, make_double2(0.0, 0.0));
   ML.assign((size_t)49 * P1 * P1, make_double2(0.0, 0.0));
   for (int q = 0; q < 4; q++) {
     // M2M: child centre relative to the parent, in child half-lengths
     cplx z0{(q & 1) ? 1.0 : -1.0, (q >> 1) ? 1.0 : -1.0};
-    double2 *op = &MM[(size_t)q * P1 * P1];
-    op[0 * P1 + 0] = make_double2(1.0, 0.0);
-    for (int l = 1; l <= p; l++) {
-      const double s = std::ldexp(1.0, -l);
-      cplx zl = cpw(z0, l);
-      op[0 * P1 + l] = make_double2(-zl.x / l * s, -zl.y / l * s);
-      for (int k = 1; k <= l; k++) {
-        cplx zz = cpw(z0, l - k);
-        double b = C[l - 1][k - 1] * s;
-        op[k * P1 + l] = make_double2(zz.x * b, zz.y * b);
-      }
+    double2 *pw = &MM[(size_t)P1 * P1 + (size_t)q * 2 * P1];
+    const cplx iz = cinv(z0), hz{0.5 * z0.x, 0.5 * z0.y};
+    for (int k = 0; k <= p; k++) {
+      const cplx a = cpw(iz, k), b = cpw(hz, k);
+      pw[k] = make_double2(a.x, a.y);
+      pw[P1 + k] = make_double2(b.x, b.y);
     }
     // L2L: child centre relative to the parent, in parent half-lengths
     cplx w0{(q & 1) ? 0.5 : -0.5, (q >> 1) ? 0.5 : -0.5};
