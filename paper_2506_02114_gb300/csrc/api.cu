@@ -133,7 +133,7 @@ struct DBuf {
 // Buffers of a handle are allocated and freed in stream order on its plan
 // stream, from the device's default memory pool, whose release threshold is
 // raised so that the memory of a destroyed handle is reused by the next one
-// instead of being returned to the driver (creating and destroying handles
+// instead of being returned to the CUDA driver (creating and destroying handles
 // of the same size then costs no driver allocation).
 struct AllocStream {
   cudaStream_t prev;
