@@ -41,8 +41,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FMA lanes x 2 flops 
 
 # dram bytes per launch of k_shoot_ipm from one ncu capture (see profiles/),
 # valid only for the kernel sources it was taken on (hash below)
-NCU_TRAFFIC = {"sources_sha1": "b9be6e3fb43b72a6e592a158c809d153cbc0fcb6",
-               "bytes_per_launch": 70.77e6 + 3.36e9}
+NCU_TRAFFIC = {"sources_sha1": "ef45a235778aeee2d9ff0ac512bfa46407d5b75d",
+               "bytes_per_launch": 68.97e6 + 3.36e9}
 
 
 def kernel_sources_sha1():

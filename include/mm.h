@@ -224,6 +224,12 @@ typedef struct {
   double ms_autotune;       /* host wall time mm_create spent tuning, 0 if none */
   int64_t triangles_near_critical; /* triangles not wholly beyond one map edge
                                with local |mu| above critical_mu (last run) */
+  uint32_t error_bits;      /* the handle's device error word: 1 quadtree
+                               invariant, 2 a vertex outside every active leaf,
+                               4 a star-rectangle corner near a sub-cell, 8 a
+                               map index out of range (only the MM_DEBUG build
+                               checks, and skips the access) */
+  int32_t reserved2;
 } mm_stats;
 
 /*

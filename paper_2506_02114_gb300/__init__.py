@@ -84,7 +84,8 @@ class Stats(ctypes.Structure):
                 ("ms_normalize", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_first_pass", ctypes.c_double), ("ms_second_pass", ctypes.c_double),
                 ("rows_per_item", ctypes.c_int32), ("autotuned", ctypes.c_int32),
-                ("ms_autotune", ctypes.c_double), ("triangles_near_critical", ctypes.c_int64)]
+                ("ms_autotune", ctypes.c_double), ("triangles_near_critical", ctypes.c_int64),
+                ("error_bits", ctypes.c_uint32), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "params"}
@@ -106,11 +107,18 @@ def library_path():
 
 
 def lib(build_if_missing=True):
-    """Load libmm.so (building it when absent or stale); raises if it cannot."""
+    """Load libmm.so (building it when absent or stale); raises if it cannot.
+    With MM_DEBUG_BUILD=1 in the environment, the MM_DEBUG variant is used
+    (bounds-checked map atomics; violations reported in
+    mm_get_stats().error_bits)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build_if_missing else _build.LIB
+    debug = os.environ.get("MM_DEBUG_BUILD") == "1"
+    if build_if_missing:
+        path = _build.build(debug=debug)
+    else:
+        path = _build.LIB_DEBUG if debug else _build.LIB
     if not os.path.exists(path):
         raise RuntimeError("libmm.so is missing: run paper_2506_02114_gb300.build.build()")
     L = ctypes.CDLL(path)

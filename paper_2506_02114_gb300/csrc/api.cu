@@ -708,6 +708,7 @@ static void fill_mapdev(mm_map *h) {
                          (h->opt.critical_mu > 0.0 ? h->opt.critical_mu : 1e3));
   M.npix = P.npix;
   M.npix_y = P.npix_y;
+  M.err = h->err.p;
   M.acc = h->acc.p;
   M.span = h->span.p;
   M.stat = h->stat.p;
@@ -1443,6 +1444,8 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
   out->ms_tree = out->ms_expansions = out->ms_shoot = out->ms_normalize = out->ms_total = -1.0;
   out->ms_first_pass = out->ms_second_pass = -1.0;
   if (h->last_stream || h->ran) CK(cudaStreamSynchronize(h->last_stream));
+  if (h->err.p)
+    CK(cudaMemcpy(&out->error_bits, h->err.p, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (h->mode != MM_PLAIN_FP64 && h->n_nodes > 0) {
     std::vector<int32_t> fc(h->n_nodes);
     CK(cudaMemcpy(fc.data(), h->first_child.p, h->n_nodes * sizeof(int32_t),

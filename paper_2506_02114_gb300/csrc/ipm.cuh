@@ -70,10 +70,26 @@ __device__ __forceinline__ unsigned long long frac_to_fixed(float f) {
 // accumulation
 // ---------------------------------------------------------------------------
 
+// MM_DEBUG builds check every accumulator and row-difference index against
+// its array before the atomic and, out of range, skip the access and set
+// ERR_BOUNDS in the error word (read back through mm_get_stats).  Other
+// builds compile the check to nothing.
+#ifdef MM_DEBUG
+__device__ __forceinline__ bool mm_index_ok(unsigned *err, long long idx, long long n) {
+  if (idx >= 0 && idx < n) return true;
+  atomicOr(err, ERR_BOUNDS);
+  return false;
+}
+#define MM_INDEX_OK(err, idx, n) mm_index_ok((err), (long long)(idx), (long long)(n))
+#else
+#define MM_INDEX_OK(err, idx, n) true
+#endif
+
 // Add v fixed-point units to map pixel (gx, gy) if it lies in the map.
 __device__ __forceinline__ void deposit(const MapDev &M, long long gx, long long gy,
                                         unsigned long long v) {
-  if (v && gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix_y)
+  if (v && gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix_y &&
+      MM_INDEX_OK(M.err, gy * M.npix + gx, (long long)M.npix * M.npix_y))
     atomicAdd(&M.acc[gy * M.npix + gx], v);
 }
 
@@ -83,6 +99,7 @@ __device__ __forceinline__ void deposit(const MapDev &M, long long gx, long long
 struct MapAcc {
   unsigned long long *acc, *span;
   int npix, npix_y;
+  unsigned *err;
 };
 
 // Lane-private run accumulator: consecutive one-pixel triangles of a lane's
@@ -93,7 +110,8 @@ struct RunAcc {
 };
 
 __device__ __forceinline__ void run_flush(const MapDev &M, RunAcc &a) {
-  if (a.idx >= 0) atomicAdd(&M.acc[a.idx], a.val);
+  if (a.idx >= 0 && MM_INDEX_OK(M.err, a.idx, (long long)M.npix * M.npix_y))
+    atomicAdd(&M.acc[a.idx], a.val);
   a.idx = -1;
   a.val = 0;
 }
@@ -105,7 +123,8 @@ __device__ __forceinline__ void run_add(const MapDev &M, RunAcc &a, long long id
     a.val += v;
     return;
   }
-  if (a.idx >= 0) atomicAdd(&M.acc[a.idx], a.val);
+  if (a.idx >= 0 && MM_INDEX_OK(M.err, a.idx, (long long)M.npix * M.npix_y))
+    atomicAdd(&M.acc[a.idx], a.val);
   a.idx = idx;
   a.val = v;
 }
@@ -507,7 +526,8 @@ __device__ __forceinline__ void pixel_task(const MapAcc &M, const RowRecs *rr, i
       sh = fmaf(rr->h[e][o], piece_mean(rr->a[e][o] - cl, rr->b[e][o] - cl), sh);
     // the row and its columns lie in the map (clamped when the row was set up)
     const unsigned long long v = frac_to_fixed(sh);
-    if (v) atomicAdd(&M.acc[(long long)rr->gy[o] * M.npix + rr->gx0[o] + c], v);
+    const long long idx = (long long)rr->gy[o] * M.npix + rr->gx0[o] + c;
+    if (v && MM_INDEX_OK(M.err, idx, (long long)M.npix * M.npix_y)) atomicAdd(&M.acc[idx], v);
   }
 }
 
@@ -520,10 +540,10 @@ __device__ __forceinline__ void pixel_task(const MapAcc &M, const RowRecs *rr, i
 // the rows differ.  Call with all 32 lanes.
 __device__ __forceinline__ void warp_tri_jobs(unsigned long long *acc,
                                                   unsigned long long *span, int npix,
-                                                  int npix_y,
+                                                  int npix_y, unsigned *err,
                                                   const TriJob *q, int nb, RowRecs *rr,
                                                   int lane) {
-  const MapAcc M = {acc, span, npix, npix_y};
+  const MapAcc M = {acc, span, npix, npix_y, err};
   int rl = 0, nrows = 0;
   if (lane < nb) {
     const TriJob &J = q[lane];
@@ -566,9 +586,13 @@ __device__ __forceinline__ void warp_tri_jobs(unsigned long long *acc,
           np -= fb - fa + 1;
           // a fully covered pixel holds 1/|area| of the triangle (< 1 when any does)
           const unsigned long long full = frac_to_fixed(fabsf(J.inv2));
-          unsigned long long *sp = M.span + (long long)(J.oy + r) * (M.npix + 1);
-          atomicAdd(&sp[J.ox + fa], full);
-          atomicAdd(&sp[J.ox + fb + 1], 0ull - full);
+          const long long row = (long long)(J.oy + r) * (M.npix + 1);
+          const long long sn = (long long)M.npix_y * (M.npix + 1);
+          if (MM_INDEX_OK(M.err, row + J.ox + fa, sn) &&
+              MM_INDEX_OK(M.err, row + J.ox + fb + 1, sn)) {
+            atomicAdd(&M.span[row + J.ox + fa], full);
+            atomicAdd(&M.span[row + J.ox + fb + 1], 0ull - full);
+          }
         }
       }
     }
@@ -659,7 +683,7 @@ __device__ __forceinline__ void jq_share(const MapDev &M, JobQueue &jq, bool flu
     } else {
       if (M.bigq_cap > 0 && lane < nb && base + lane < (unsigned long long)M.bigq_cap)
         M.bigq[base + lane] = empty_job_impl();
-      warp_tri_jobs(M.acc, M.span, M.npix, M.npix_y, jq.q + jq.n, nb, jq.rr, lane);
+      warp_tri_jobs(M.acc, M.span, M.npix, M.npix_y, M.err, jq.q + jq.n, nb, jq.rr, lane);
     }
   }
 }

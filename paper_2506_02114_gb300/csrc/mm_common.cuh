@@ -28,6 +28,8 @@ enum : unsigned int {
   ERR_LOOKUP = 2u,            // a ray vertex fell outside every active leaf
   ERR_RECT_CORNER = 4u,       // a record's rectangular-sheet series converges too
                               // slowly (a star-rectangle corner is near it)
+  ERR_BOUNDS = 8u,            // MM_DEBUG builds: a map or row-difference index out of
+                              // range (the access was skipped)
 };
 
 // Per sub-cell of an active leaf: everything a ray vertex in it needs (64
@@ -106,6 +108,7 @@ struct MapDev {
                               // triangle counts as near-critical
   // map
   int32_t npix, npix_y;       // pixels along x (row length) and y (rows)
+  unsigned *err;              // the handle's error word
   unsigned long long *acc;    // npix_y*npix fixed point, 2^32 = one triangle
   unsigned long long *span;   // npix_y*(npix+1) row difference array
   // statistics (per map)

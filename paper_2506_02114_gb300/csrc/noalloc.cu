@@ -144,6 +144,7 @@ extern "C" mm_status mm_map_plain_fp64_noalloc(
   md.rows_per_item = 64;
   md.npix = npix;
   md.npix_y = npix;  // square map
+  md.err = err;
   md.acc = acc;
   md.span = span;
   md.stat = stat;

@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(256, MM_BIG_MINB) k_big_ipm(const MapDev M) {
     const int nb = (int)min(32ll, n - base);
     if (lane < nb) q[w][lane] = M.bigq[base + lane];
     __syncwarp();
-    warp_tri_jobs(M.acc, M.span, M.npix, M.npix_y, q[w], nb, &rr[w], lane);
+    warp_tri_jobs(M.acc, M.span, M.npix, M.npix_y, M.err, q[w], nb, &rr[w], lane);
   }
 }
 

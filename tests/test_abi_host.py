@@ -141,3 +141,15 @@ def test_create_rejects_a_bad_star_rectangle():
         with pytest.raises(mm.MMError) as e:
             mm.create(0.3, 0.1, 0.0, m, pos, 1.0, 16, 1.0, star_rect=rect)
         assert e.value.status == mm.MM_EINVAL
+
+
+def test_debug_variant_builds_and_exports_every_symbol():
+    """The MM_DEBUG build (bounds-checked map atomics) compiles for sm_103a
+    into its own directory and exports the same C ABI."""
+    import ctypes
+    from paper_2506_02114_gb300 import build as B
+    path = B.build(debug=True)
+    assert path == B.LIB_DEBUG and path != B.LIB
+    L = ctypes.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(L, n), n
