@@ -56,11 +56,13 @@ def kernel_sources_sha1():
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-one-core", action="store_true",
+                    help="skip the one-core oracle run beside the all-core one")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (the default is the one the metric is quoted on)")
     ap.add_argument("--rays-per-pixel", type=float, default=None,
@@ -168,6 +170,21 @@ def oracle_rays_per_s(wl, m, pos, seconds, nthreads=None):
                                  % (rows, p.n[0], wl.name, len(m))}
 
 
+def oracle_one_core(wl, m, pos):
+    """The oracle on one host core over the smallest sample it takes (one
+    cell row, full width): the per-core rate beside the all-core one."""
+    import oracle
+    p = oracle.derive_params(wl.kappa, wl.gamma, wl.s, m, wl.half_length, wl.npix,
+                             rays_per_pixel=wl.rays_per_pixel)
+    mid = (p.n[1] - 1) // 2
+    t0 = time.perf_counter()
+    oracle.magnification_map(p, m, pos, mid, mid + 1, nthreads=1)
+    dt = time.perf_counter() - t0
+    rays = 2 * p.n[0]
+    return {"value": rays / dt, "unit": UNIT, "cores": 1, "pairs_per_s": rays * len(m) / dt,
+            "sample": "1 cell row x %d rays (full width, all %d stars)" % (p.n[0], len(m))}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -189,7 +206,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": info["sample"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-                         "sample": info["sample"]},
+                         "sample": info["sample"], "pairs_per_s": value * len(m)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -346,8 +363,14 @@ def run_native(args):
     cpu = None
     if not (args.no_cpu_baseline or args.kernel_only) and world == 1:
         v, info = oracle_rays_per_s(wl, m, pos, args.cpu_seconds)
+        # a direct sum evaluates every star for every ray: pairs = rays x stars
         cpu = {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-               "sample": info["sample"]}
+               "sample": info["sample"], "pairs_per_s": v * len(m)}
+        # the one-core leg takes one full-width cell row; skipped where that
+        # would take more than ~30 s at the all-core rate per core
+        est_s = 2 * st["params"]["n"][0] / (v / info["cores"])
+        if not args.no_one_core and est_s <= 30.0:
+            cpu["one_core"] = oracle_one_core(wl, m, pos)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -362,6 +385,8 @@ def run_native(args):
                    "autotuned": st["autotuned"], "mapping": "irs" if args.irs else "ipm",
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
+        "step_ms": {"median": statistics.median(ms), "mean": float(np.mean(ms)),
+                    "std": float(np.std(ms)), "min": min(ms), "max": max(ms)},
         "maps_per_s": world / (ms_per_step * 1e-3),
         "stages_ms": {k: st[k] for k in ("ms_tree", "ms_expansions", "ms_shoot", "ms_first_pass",
                                          "ms_second_pass", "ms_normalize", "ms_total")},
