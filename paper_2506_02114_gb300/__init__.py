@@ -272,12 +272,27 @@ def run_batch(hs, stream=None):
 def get_map(h: Handle, out=None):
     """Magnification map.  out=None: new numpy (npix_y, npix) float32 array.
     out may be a torch CUDA float32 tensor with npix_y*npix elements."""
-    if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+    n = h.npix_y * h.npix
+    if out is not None and hasattr(out, "is_cuda"):
+        if not out.is_cuda:
+            out_np = out.numpy()          # a CPU tensor shares its storage
+            _check_out(out_np, n)
+            _check(lib().mm_get_map(h.ptr, out_np.ctypes.data_as(_vp), 0))
+            return out
+        if str(out.dtype) != "torch.float32" or out.numel() != n or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 tensor of %d elements" % n)
         _check(lib().mm_get_map(h.ptr, _vp(out.data_ptr()), 1))
         return out
     a = np.empty((h.npix_y, h.npix), dtype=np.float32) if out is None else out
+    _check_out(a, n)
     _check(lib().mm_get_map(h.ptr, a.ctypes.data_as(_vp), 0))
     return a
+
+
+def _check_out(a, n):
+    if (not isinstance(a, np.ndarray) or a.dtype != np.float32 or a.size != n
+            or not a.flags.c_contiguous or not a.flags.writeable):
+        raise ValueError("out must be a writeable C-contiguous float32 array of %d elements" % n)
 
 
 def get_map_fixed(h: Handle):
@@ -302,6 +317,9 @@ def map_plain_fp64_noalloc(kappa, gamma, s, masses_dev, pos_dev, half_length, np
     pos_dev ((n, 2) or (2n,)) and map_out_dev (npix*npix float32) are CUDA
     tensors; the grid arguments are host sequences.  Asynchronous."""
     n = int(masses_dev.numel())
+    _check_dev(masses_dev, "torch.float64", n, "masses_dev")
+    _check_dev(pos_dev, "torch.float64", 2 * n, "pos_dev")
+    _check_dev(map_out_dev, "torch.float32", int(npix) * int(npix), "map_out_dev", at_least=True)
     rg = (ctypes.c_int64 * 2)(int(ray_grid[0]), int(ray_grid[1]))
     org = (ctypes.c_double * 2)(float(grid_origin[0]), float(grid_origin[1]))
     hh = (ctypes.c_double * 2)(float(grid_spacing[0]), float(grid_spacing[1]))
@@ -312,6 +330,14 @@ def map_plain_fp64_noalloc(kappa, gamma, s, masses_dev, pos_dev, half_length, np
         ctypes.cast(cy, _dp), rg, ctypes.cast(org, _dp), ctypes.cast(hh, _dp),
         _vp(map_out_dev.data_ptr()), _vp(current_stream() if stream is None else stream)))
     return map_out_dev
+
+
+def _check_dev(t, dtype, numel, name, at_least=False):
+    size_ok = int(t.numel()) >= numel if at_least else int(t.numel()) == numel
+    if not getattr(t, "is_cuda", False) or str(t.dtype) != dtype or not size_ok \
+            or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA %s tensor of %s%d elements"
+                         % (name, dtype[len("torch."):], "at least " if at_least else "", numel))
 
 
 def shard_rows(n_rows, rank, world):

@@ -153,3 +153,24 @@ def test_debug_variant_builds_and_exports_every_symbol():
     L = ctypes.CDLL(path)
     for n in declared_functions():
         assert hasattr(L, n), n
+
+
+def test_binding_rejects_output_buffers_of_the_wrong_shape():
+    """The binding checks caller buffers before the C library writes into
+    them: size, dtype, contiguity, writeability and device."""
+    import torch
+    h = mm.Handle(None, 4, 3)
+    for bad in (np.empty(11, np.float32), np.empty(12, np.float64),
+                np.empty((3, 8), np.float32)[:, ::2], torch.empty(13, dtype=torch.float32)):
+        with pytest.raises(ValueError):
+            mm.get_map(h, bad)
+    ro = np.empty((3, 4), np.float32)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        mm.get_map(h, ro)
+    h.ptr = None
+    cpu = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="masses_dev"):
+        mm.map_plain_fp64_noalloc(0.4, 0.3, 0.0, cpu, torch.zeros(8, dtype=torch.float64), 4.0,
+                                  16, (8, 8), (-1.0, -1.0), (0.25, 0.25),
+                                  torch.zeros(256, dtype=torch.float32))
