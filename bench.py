@@ -336,19 +336,24 @@ def run_native(args):
     # roofline of the hot kernel, the fused deflection + first mapping pass
     # (FP32 ALU bound); the second pass deals the queued larger triangles
     p, pe = st["fmm_order"], st["eval_order"]
-    # near field + local expansion (p_e terms about the sub-cell centre) + macro + IPM test
-    flops_per_ray = 11.0 * st["mean_near_stars"] + 8.0 * (pe - 1) + 8.0 + 20.0
+    # near field + local expansion (p_e terms about the sub-cell centre) + macro, then the
+    # mapping: the polygon-mapping size test (~20) or the ray's pixel index (~4)
+    flops_per_ray = (11.0 * st["mean_near_stars"] + 8.0 * (pe - 1) + 8.0
+                     + (4.0 if args.irs else 20.0))
     shoot_s = float(np.mean(first_ms)) * 1e-3
     # vertices whose deflection culling proved unnecessary are not computed:
     # a culled warp row skips the 31 vertex columns of its work item
     computed = max(0, rays - 31 * st["rows_culled"])
     achieved = computed * flops_per_ray / shoot_s / 1e12
+    # DRAM bytes of one full-size launch, taken by ncu for the polygon-mapping
+    # kernel only; none recorded for the ray-counting kernel
     traffic = None
-    if NCU_TRAFFIC["sources_sha1"] == kernel_sources_sha1():
+    if not args.irs and NCU_TRAFFIC["sources_sha1"] == kernel_sources_sha1():
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "k_shoot_ipm", "flops_per_ray": flops_per_ray,
+                "kernel": "k_shoot_irs" if args.irs else "k_shoot_ipm",
+                "flops_per_ray": flops_per_ray,
                 "rays_computed": computed,
                 "kernel_ms": shoot_s * 1e3,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
