@@ -174,3 +174,25 @@ def test_binding_rejects_output_buffers_of_the_wrong_shape():
         mm.map_plain_fp64_noalloc(0.4, 0.3, 0.0, cpu, torch.zeros(8, dtype=torch.float64), 4.0,
                                   16, (8, 8), (-1.0, -1.0), (0.25, 0.25),
                                   torch.zeros(256, dtype=torch.float32))
+
+
+def test_non_finite_inputs_rejected_before_touching_a_gpu():
+    """Injected faults on the host: a NaN or infinite star position or mass,
+    a zero mass, and non-finite lens parameters each return MM_EINVAL from
+    mm_create's validation, before any device work."""
+    m, pos = synthetic.star_field(1, 60, 12.0)
+    cases = []
+    for i, v in ((0, float("nan")), (7, float("inf")), (59, -float("inf"))):
+        p = pos.copy()
+        p[i, i % 2] = v
+        cases.append((m, p, 0.3))
+    for v in (float("nan"), float("inf"), 0.0):
+        mm_ = m.copy()
+        mm_[3] = v
+        cases.append((mm_, pos, 0.3))
+    cases.append((m, pos, float("nan")))
+    for masses, positions, kappa in cases:
+        with pytest.raises(mm.MMError) as e:
+            mm.create(kappa, 0.1, 0.0, masses, positions, 1.0, 16, img_half=(2.0, 2.0),
+                      ray_grid=(8, 8))
+        assert e.value.status == mm.MM_EINVAL, str(e.value)
