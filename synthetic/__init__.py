@@ -180,8 +180,11 @@ class Workload:
 
 
 def workload(name: str) -> Workload:
-    """The five workloads: radii/N_star/rays-per-pixel are fixed numbers here
-    (their derivation is recorded in the design doc); seeds are 1000 + index."""
+    """The five workloads.  Radii, star counts and rays per pixel are fixed
+    numbers here: a disk radius of 1.1 x the shooting region's half-diagonal
+    (or the radius that holds a fixed star count at kappa_star), and rays per
+    pixel ~100 / |mu_macro| so that ~100 rays land per pixel.  Seeds are
+    1000 + index."""
     if name == "plain_fp64_160":
         # 160 equal stars in a disk of radius 20; kappa=0.4, gamma=0.3, s=0;
         # explicit 700 x 2000 ray grid over image half-widths (16/3, 16);
