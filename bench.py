@@ -288,10 +288,12 @@ def run_native(args):
 
     fp64_plain, e2e = None, None
     if not args.kernel_only:
-        # plain FP64 direct sum on the same GPU: a band of rows sized to ~1 s
+        # plain FP64 direct sum on the same GPU: a band of full-width rows of
+        # at least ~1e6 rays, longer where that takes under ~1 s
         n0 = st["params"]["n"][0]
         pairs_per_s = 4e10
-        band = int(max(2, min(st["params"]["n"][1] - 1, pairs_per_s / (n0 * len(m)))))
+        band = int(max(2, min(st["params"]["n"][1] - 1,
+                              max(math.ceil(1.05e6 / n0), pairs_per_s / (n0 * len(m))))))
         r0 = (st["params"]["n"][1] - 1) // 2 - band // 2
         hp = mm.create(*args_map, mode=mm.MM_PLAIN_FP64, time_stages=True, row_begin=r0,
                        row_end=r0 + band)
