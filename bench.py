@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="--impl reference: oracle seconds per step (default: ~100 s "
+                         "spread over the steps, 2 to 30 s each)")
     ap.add_argument("--no-one-core", action="store_true",
                     help="skip the one-core oracle run beside the all-core one")
     ap.add_argument("--workload", default=WORKLOAD,
@@ -191,7 +194,8 @@ def run_reference(args):
         return 0
     wl = synthetic.workload(WORKLOAD)
     m, pos = wl.stars()
-    per_step = max(2.0, min(30.0, 100.0 / max(1, args.steps + args.warmup)))
+    per_step = (args.ref_seconds if args.ref_seconds is not None
+                else max(2.0, min(30.0, 100.0 / max(1, args.steps + args.warmup))))
     vals = []
     info = None
     for k in range(args.warmup + args.steps):
