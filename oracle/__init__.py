@@ -87,6 +87,11 @@ def lib():
         L.or_map_from_vertices.argtypes = [ctypes.POINTER(Params), _dp, ctypes.c_int64,
                                            ctypes.c_int64, _dp, _dp,
                                            ctypes.POINTER(MapStats), ctypes.c_int]
+        L.or_map_tile_from_vertices.restype = ctypes.c_int
+        L.or_map_tile_from_vertices.argtypes = [ctypes.POINTER(Params), _dp, ctypes.c_int64,
+                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                _dp, _dp, ctypes.POINTER(MapStats),
+                                                ctypes.c_int]
         L.or_irs_tile.restype = ctypes.c_int
         L.or_irs_tile.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _dp, _dp,
                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -212,6 +217,27 @@ def map_from_vertices(params: Params, w_xy, row_begin, row_end, nthreads=None):
     if rc != 0:
         raise ValueError("oracle: bad row range")
     return mu, acc, {"triangles": st.triangles, "dropped": st.dropped, "pieces": st.pieces}
+
+
+def map_tile_from_vertices(params: Params, w_xy, row_begin, row_end, col_begin, col_end,
+                           nthreads=None):
+    """IPM only: map of the cells of rows [row_begin, row_end) and columns
+    [col_begin, col_end) from the source positions of their vertices (rows
+    row_begin..row_end, columns col_begin..col_end inclusive, row-major)."""
+    w = _f64(w_xy).reshape(-1, 2)
+    if w.shape[0] != (row_end - row_begin + 1) * (col_end - col_begin + 1):
+        raise ValueError("oracle: vertex array does not match the tile")
+    n, ny = params.npix, params.npix_y
+    mu = np.zeros((ny, n), dtype=np.float64)
+    acc = np.zeros((ny, n), dtype=np.float64)
+    st = MapStats()
+    rc = lib().or_map_tile_from_vertices(ctypes.byref(params), _ptr(w), int(row_begin),
+                                         int(row_end), int(col_begin), int(col_end),
+                                         mu.ctypes.data_as(_dp), acc.ctypes.data_as(_dp),
+                                         ctypes.byref(st), nthreads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle: bad tile")
+    return mu, {"triangles": st.triangles, "dropped": st.dropped, "pieces": st.pieces}
 
 
 def irs_map(params: Params, masses, pos_xy, row_begin=0, row_end=-1, col_begin=0,

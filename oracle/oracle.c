@@ -414,6 +414,14 @@ int or_map_from_vertices(const or_params *p, const double *w_xy,
                                 acc_out, stats, nthreads);
 }
 
+int or_map_tile_from_vertices(const or_params *p, const double *w_xy, int64_t row_begin,
+                              int64_t row_end, int64_t col_begin, int64_t col_end,
+                              double *mu_out, double *acc_out, or_map_stats *stats,
+                              int nthreads) {
+  return map_tile_from_vertices(p, w_xy, row_begin, row_end, col_begin, col_end, mu_out,
+                                acc_out, stats, nthreads);
+}
+
 int or_map_tile(const or_params *p, int64_t n_stars, const double *masses,
                 const double *pos_xy, int64_t row_begin, int64_t row_end,
                 int64_t col_begin, int64_t col_end, double *mu_out, double *acc_out,

@@ -119,6 +119,14 @@ int or_map_from_vertices(const or_params *p, const double *w_xy,
                          double *mu_out, double *acc_out, or_map_stats *stats,
                          int nthreads);
 
+/* Same as or_map_tile but from precomputed source positions w_xy of the
+ * vertices of rows [row_begin, row_end] and columns [col_begin, col_end]
+ * (both inclusive), row-major, (col_end-col_begin+1) points per row. */
+int or_map_tile_from_vertices(const or_params *p, const double *w_xy, int64_t row_begin,
+                              int64_t row_end, int64_t col_begin, int64_t col_end,
+                              double *mu_out, double *acc_out, or_map_stats *stats,
+                              int nthreads);
+
 /* Inverse ray shooting over the vertices of rows [row_begin, row_end] and
  * columns [col_begin, col_end] (both inclusive; row_end < 0 or col_end < 0
  * means up to the grid's last vertex): counts (npix_y rows of npix, may be NULL) gets

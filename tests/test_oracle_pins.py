@@ -513,3 +513,21 @@ def test_non_square_map(oracle_mod):
     cx = axis(1 - kappa + gamma, 2.5, 41, -Fr(hl), nx)
     cy = axis(1 - kappa - gamma, 3.5, 57, -hy, ny)
     np.testing.assert_array_equal(cnt, np.outer(cy, cx))
+
+
+def test_tile_map_from_vertices_equals_the_tile_map(oracle_mod):
+    """map_tile_from_vertices (the polygon mapping of given source positions,
+    used to write the stored tile maps) apportions exactly what the direct
+    tile map does: same vertices in, same map out."""
+    m, pos = synthetic.star_field(61, 80, 9.0)
+    p = oracle_mod.derive_params(0.45, 0.3, 0.4, m, 1.5, 40, rays_per_pixel=6.0,
+                                 flux_fraction_f=0.01)
+    r0, r1, c0, c1 = 40, 77, 13, 58
+    ii, jj = np.meshgrid(np.arange(c0, c1 + 1), np.arange(r0, r1 + 1))
+    w = oracle_mod.deflect(p, m, pos, oracle_mod.grid_vertices(p, ii.ravel(), jj.ravel()))
+    a, sa = oracle_mod.map_tile_from_vertices(p, w, r0, r1, c0, c1)
+    b, sb = oracle_mod.magnification_map_tile(p, m, pos, r0, r1, c0, c1)
+    assert sa == sb and sa["triangles"] == 2 * (r1 - r0) * (c1 - c0)
+    np.testing.assert_array_equal(a, b)
+    with pytest.raises(ValueError):
+        oracle_mod.map_tile_from_vertices(p, w[:-1], r0, r1, c0, c1)
