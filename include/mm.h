@@ -265,9 +265,14 @@ mm_status mm_derive_params(double kappa_tot, double shear, double smooth_fractio
  *
  * Errors: MM_EINVAL for |(1-kappa)^2 - gamma^2| < 1e-12, s outside [0,1],
  * kappa_star > 0 with no stars, masses <= 0 or non-finite positions, npix < 1,
- * half_length <= 0, fmm_order or leaf_size out of range, a shooting region
- * not inside the stars' bounding box (unless img_half is explicit), or a ray
- * grid above 2^31 rays per axis; MM_ENOMEM / MM_ECUDA otherwise.
+ * half_length <= 0, fmm_order or leaf_size out of range, a ray grid above
+ * 2^31 rays per axis, or (kappa_star > 0, img_half not explicit) a ray grid
+ * the stars do not cover: its box must lie inside the stars' bounding box
+ * and, for a star disk (no star_rect), each of its four corners within the
+ * disk the stars fill, radius max |z_i| about the origin -- the circular
+ * sheet deflects by -kappa_star z only inside that disk (Sec. 3.1).  With
+ * star_rect the grid must lie strictly inside the rectangle instead.
+ * MM_ENOMEM / MM_ECUDA otherwise.
  */
 mm_status mm_create(double kappa_tot, double shear, double smooth_fraction,
                     int64_t n_stars, const double *masses, const double *pos_xy,
@@ -297,6 +302,40 @@ mm_status mm_run(mm_map *h, void *stream);
  * its own mm_run.
  */
 mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream);
+
+/*
+ * Run the map over a rectangle of the handle's cells only: cell rows
+ * [row_begin, row_end) and columns [col_begin, col_end) of the ray grid,
+ * inside the handle's own rows and columns (mm_options row/column band).
+ * The plan mm_create made for the whole handle -- tree, expansions, leaf
+ * records, lookup grid, culling bounds, second-pass queue -- is used
+ * unchanged, and each triangle's contribution depends only on its vertices,
+ * so the fixed-point maps (mm_get_map_fixed) of rectangles that partition the
+ * handle's cells add up bit for bit to mm_run's map.  This is how one map is
+ * sharded over devices by ray-grid bands (Sec. 6 names several GPUs as the
+ * remaining speed-up): each device runs its band on its own handle, the u64
+ * maps are summed (integer sums, exact in any order) and mm_normalize_fixed
+ * turns the sum into magnification.  It also lets a full-size plan be
+ * checked tile by tile.  Asynchronous like mm_run; afterwards mm_get_map,
+ * mm_get_map_fixed and mm_get_stats describe this rectangle's run.  In
+ * MM_FMM_IRS mode the rays counted are the rectangle's vertices, its last
+ * row and column included.  MM_EINVAL for an empty rectangle or one outside
+ * the handle's cells.
+ */
+mm_status mm_run_cells(mm_map *h, int64_t row_begin, int64_t row_end, int64_t col_begin,
+                       int64_t col_end, void *stream);
+
+/*
+ * Normalise a fixed-point accumulator into magnification with the handle's
+ * scale (Sec. 3.2: mu = acc 2^-32 (h_x h_y / 2) / delta^2 for polygon
+ * mapping; count h_x h_y / delta^2 for ray counting).  acc: DEVICE pointer
+ * to npix_y rows of npix uint64, as mm_get_map_fixed returns them or their
+ * sum over several handles of the same map (mm_run_cells bands); out: DEVICE
+ * pointer to npix_y * npix floats.  Bit-identical to mm_get_map's values for
+ * the same accumulator.  Enqueued on `stream`; the caller keeps both buffers
+ * alive until it completes.
+ */
+mm_status mm_normalize_fixed(const mm_map *h, const uint64_t *acc, float *out, void *stream);
 
 /*
  * Copy the magnification map (npix_y rows of npix floats) into out.  on_device = 0:
@@ -333,24 +372,30 @@ mm_status mm_get_stats(const mm_map *h, mm_stats *out);
  *
  * Computes the same map as mm_create(mode = MM_PLAIN_FP64, explicit ray
  * grid) + mm_run + mm_get_map(on_device = 1): direct FP64 sum over every star
- * for each ray vertex, then inverse polygon mapping, on `stream`
- * (asynchronous; synchronise before reading map_out).
+ * for each ray vertex, then inverse polygon mapping, on `stream`.  The call
+ * returns once the map is complete: it synchronises `stream` to read the
+ * kernels' error word, and returns MM_ECUDA (map_out not valid) when a
+ * kernel reported an error (the MM_DEBUG build's index checks).
  *
  *   kappa_tot, shear, smooth_fraction: as in mm_create.
- *   masses[n_stars], pos_xy[2*n_stars]: DEVICE pointers, interleaved (x, y).
+ *   masses[n_stars], pos_xy[2*n_stars]: DEVICE pointers of the current
+ *     device (or managed memory), interleaved (x, y).  Host pointers and
+ *     other devices' buffers are rejected with MM_EINVAL before any work.
  *   half_length, npix, center_y[2] (host, may be NULL = origin): the map.
  *   ray_grid[2] (host): rays per axis; grid_origin[2], grid_spacing[2]
  *     (host): image-plane position of vertex (0, 0) and the ray spacings,
  *     e.g. mm_params.n, .x0 and .h of an equivalent handle.
- *   map_out: DEVICE pointer, npix*npix floats, row-major, row = y (square
- *     maps only).
+ *   map_out: DEVICE pointer of the current device, npix*npix floats,
+ *     row-major, row = y (square maps only).
  *
  * Scratch lives in one fixed device array inside the library (about 9.5 MB,
  * held by every GPU that loads it until the process exits), so sizes are
  * bounded: n_stars <= 16384, npix <= 256, ray_grid[0]*ray_grid[1] <= 2^19;
  * larger requests return MM_EINVAL with a message and do nothing.  The first
  * call on each device looks up that array's device address (with the device
- * current); make that first call before any stream capture.  All calls share
+ * current) and keeps it for the life of the process; make that first call
+ * before any stream capture.  cudaDeviceReset() on a device invalidates the
+ * kept address: do not call this entry point on a device after resetting it.  All calls share
  * the array and each call clears what it accumulates, so calls whose work
  * overlaps on the GPU (different streams, or different host threads) race and
  * corrupt each other's maps: serialise them.  No cudaMalloc, cudaFree or
@@ -361,6 +406,29 @@ mm_status mm_map_plain_fp64_noalloc(double kappa_tot, double shear, double smoot
                                     double half_length, int32_t npix, const double *center_y,
                                     const int64_t *ray_grid, const double *grid_origin,
                                     const double *grid_spacing, float *map_out, void *stream);
+
+/*
+ * Measured peaks for the rooflines of this library's kernels (the paper has
+ * no counterpart).  Each kind is a short microbenchmark on the current
+ * device: one warm-up launch, then the best of three launches timed with
+ * CUDA events on `stream` (synchronous).
+ *   MM_PEAK_FP32_FMA:  8 independent fmaf chains per thread, 8 blocks of 256
+ *                      threads per SM; *value in TFLOP/s (2 flops per FMA).
+ *   MM_PEAK_FP64_FMA:  the same in double; TFLOP/s.
+ *   MM_PEAK_L2_RED_U64: each thread adds 1 to 2048 scattered 64-bit words of
+ *                      a 32 MiB array (L2-resident) with an atomic add whose
+ *                      result is unused, the form of the map's fixed-point
+ *                      accumulation; *value in 1e9 reductions per second.
+ * ms (may be NULL) receives the timed launch's duration.  The call allocates
+ * (and frees) its 32 MiB array with cudaMalloc.
+ */
+typedef enum {
+  MM_PEAK_FP32_FMA = 0,
+  MM_PEAK_FP64_FMA = 1,
+  MM_PEAK_L2_RED_U64 = 2
+} mm_peak_kind;
+
+mm_status mm_measure_peak(int32_t kind, double *value, double *ms, void *stream);
 
 /* Thread-local message describing the last failed call ("" if none). */
 const char *mm_last_error(void);

@@ -93,9 +93,12 @@ class Stats(ctypes.Structure):
         return d
 
 
-EXPORTS = ["mm_derive_params", "mm_create", "mm_run", "mm_run_batch", "mm_get_map",
-           "mm_get_map_fixed", "mm_shoot_points", "mm_get_stats", "mm_map_plain_fp64_noalloc",
-           "mm_last_error", "mm_destroy"]
+EXPORTS = ["mm_derive_params", "mm_create", "mm_run", "mm_run_cells", "mm_run_batch",
+           "mm_get_map", "mm_get_map_fixed", "mm_normalize_fixed", "mm_shoot_points",
+           "mm_get_stats", "mm_map_plain_fp64_noalloc", "mm_measure_peak", "mm_last_error",
+           "mm_destroy"]
+
+MM_PEAK_FP32_FMA, MM_PEAK_FP64_FMA, MM_PEAK_L2_RED_U64 = 0, 1, 2
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -134,6 +137,13 @@ def lib(build_if_missing=True):
                             ctypes.POINTER(_vp)]
     L.mm_run.restype = ctypes.c_int
     L.mm_run.argtypes = [_vp, _vp]
+    L.mm_run_cells.restype = ctypes.c_int
+    L.mm_run_cells.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                               ctypes.c_int64, _vp]
+    L.mm_normalize_fixed.restype = ctypes.c_int
+    L.mm_normalize_fixed.argtypes = [_vp, _vp, _vp, _vp]
+    L.mm_measure_peak.restype = ctypes.c_int
+    L.mm_measure_peak.argtypes = [ctypes.c_int32, _dp, _dp, _vp]
     L.mm_run_batch.restype = ctypes.c_int
     L.mm_run_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, _vp]
     L.mm_get_map.restype = ctypes.c_int
@@ -263,6 +273,13 @@ def run(h: Handle, stream=None):
     _check(lib().mm_run(h.ptr, _vp(current_stream() if stream is None else stream)))
 
 
+def run_cells(h: Handle, row_begin, row_end, col_begin, col_end, stream=None):
+    """Run the map over cell rows [row_begin, row_end) and columns
+    [col_begin, col_end) only, with the handle's whole plan (mm_run_cells)."""
+    _check(lib().mm_run_cells(h.ptr, int(row_begin), int(row_end), int(col_begin),
+                              int(col_end), _vp(current_stream() if stream is None else stream)))
+
+
 def run_batch(hs, stream=None):
     arr = (_vp * len(hs))(*[x.ptr for x in hs])
     _check(lib().mm_run_batch(arr, len(hs),
@@ -295,11 +312,40 @@ def _check_out(a, n):
         raise ValueError("out must be a writeable C-contiguous float32 array of %d elements" % n)
 
 
-def get_map_fixed(h: Handle):
-    """Raw fixed-point accumulator (npix_y, npix) uint64: sum of round(frac*2^32)."""
+def get_map_fixed(h: Handle, out=None):
+    """Raw fixed-point accumulator (npix_y, npix) uint64: sum of round(frac*2^32).
+    out may be a contiguous CUDA int64 tensor of npix_y*npix elements (the
+    same 64 bits; enqueued on the handle's last stream)."""
+    n = h.npix_y * h.npix
+    if out is not None:
+        _check_dev(out, "torch.int64", n, "out")
+        _check(lib().mm_get_map_fixed(h.ptr, _vp(out.data_ptr()), 1))
+        return out
     a = np.empty((h.npix_y, h.npix), dtype=np.uint64)
     _check(lib().mm_get_map_fixed(h.ptr, a.ctypes.data_as(_vp), 0))
     return a
+
+
+def normalize_fixed(h: Handle, acc, out, stream=None):
+    """Magnification from a fixed-point accumulator (mm_normalize_fixed):
+    acc a contiguous CUDA int64 tensor of npix_y*npix elements (the u64 bits,
+    e.g. the sum of several bands' maps), out a CUDA float32 tensor of as many.
+    Enqueued on `stream` (torch's current stream by default)."""
+    n = h.npix_y * h.npix
+    _check_dev(acc, "torch.int64", n, "acc")
+    _check_dev(out, "torch.float32", n, "out")
+    _check(lib().mm_normalize_fixed(h.ptr, _vp(acc.data_ptr()), _vp(out.data_ptr()),
+                                    _vp(current_stream() if stream is None else stream)))
+    return out
+
+
+def measure_peak(kind, stream=None):
+    """(value, ms) of one of the MM_PEAK_* microbenchmarks on the current
+    device: TFLOP/s for the FMA kinds, 1e9 u64 reductions/s for the L2 kind."""
+    v, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mm_measure_peak(int(kind), ctypes.byref(v), ctypes.byref(ms),
+                                 _vp(current_stream() if stream is None else stream)))
+    return v.value, ms.value
 
 
 def shoot_points(h: Handle, z_xy):
@@ -338,6 +384,10 @@ def _check_dev(t, dtype, numel, name, at_least=False):
             or not t.is_contiguous():
         raise ValueError("%s must be a contiguous CUDA %s tensor of %s%d elements"
                          % (name, dtype[len("torch."):], "at least " if at_least else "", numel))
+    import torch
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError("%s is on cuda:%s, not the current device cuda:%d"
+                         % (name, t.device.index, torch.cuda.current_device()))
 
 
 def shard_rows(n_rows, rank, world):

@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "libmm.so")
 OUT_DIR_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(OUT_DIR_DEBUG, "libmm.so")
 
-SOURCES = ["api.cu", "tree.cu", "fmm.cu", "shoot.cu", "direct64.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "tree.cu", "fmm.cu", "shoot.cu", "direct64.cu", "noalloc.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

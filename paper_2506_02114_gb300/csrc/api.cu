@@ -796,8 +796,37 @@ static mm_status prepare(mm_map *h, cudaStream_t st) {
   return MM_OK;
 }
 
-static mm_status run_one(mm_map *h, cudaStream_t st) {
+// A rectangle of cells [r0, r1) x [c0, c1) of the ray grid.
+struct CellRect {
+  int64_t r0, r1, c0, c1;
+};
+
+// The handle's descriptor restricted to the cells of `r` (the plan -- tree,
+// expansions, lookup, culling bounds, queue -- is unchanged).
+static MapDev restrict_mapdev(const mm_map *h, const CellRect &r) {
+  MapDev m = h->md;
+  m.row_begin = r.r0;
+  m.row_end = r.r1;
+  m.col_begin = r.c0;
+  m.col_end = r.c1;
+  m.strips = (int32_t)((r.c1 - r.c0 + MM_STRIP - 1) / MM_STRIP);
+  m.row_blocks = (r.r1 - r.r0 + h->rows_per_item - 1) / h->rows_per_item;
+  return m;
+}
+
+// First-pass segments for `cells` cells: about one larger triangle per 12
+// cells must fit the queue (maps that fit L2, polygon mapping only).
+static int64_t segments_for(const mm_map *h, int64_t cells) {
+  if (h->segments <= 1 || h->bigq_cap <= 0) return 1;
+  return std::max<int64_t>(1, (cells / 12 + h->bigq_cap - 1) / h->bigq_cap);
+}
+
+// One run of the handle's map over its cells, or over the rectangle `rect`
+// of them (NULL: all).
+static mm_status run_one(mm_map *h, cudaStream_t st, const CellRect *rect = nullptr) {
   const mm_params &P = h->P;
+  const CellRect all = {h->row_lo, h->row_hi, h->col_lo, h->col_hi};
+  const CellRect R = rect ? *rect : all;
   h->launches = 0;
   CKS(record(h, 0, st));
   CKS(clear_map(h, st));
@@ -817,11 +846,10 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
     C.delta = P.delta;
     C.rect_c1 = h->opt.star_rect[0];
     C.rect_c2 = h->opt.star_rect[1];
-    LCH(launch_direct64_vertices(h->sx.p, h->sy.p, h->sm.p, h->N, C, h->col_lo,
-                                 h->col_hi - h->col_lo + 1, h->row_lo, h->row_hi, h->verts.p,
-                                 st));
-    LCH(launch_ipm_vertices(h->d_md.p, h->verts.p, h->col_hi - h->col_lo + 1, h->row_lo,
-                            h->row_hi, h->counter.p, h->err.p, shoot_grid(), st));
+    LCH(launch_direct64_vertices(h->sx.p, h->sy.p, h->sm.p, h->N, C, R.c0, R.c1 - R.c0 + 1,
+                                 R.r0, R.r1, h->verts.p, st));
+    LCH(launch_ipm_vertices(h->d_md.p, h->verts.p, R.c1 - R.c0 + 1, R.r0, R.r1, h->counter.p,
+                            h->err.p, shoot_grid(), st));
     CKS(record(h, 5, st));
     LCH(launch_big_ipm(h->md, st));
   } else {
@@ -834,10 +862,11 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
       CKS(prepare(h, st));
     }
     CKS(record(h, 2, st));
+    const MapDev base = rect ? restrict_mapdev(h, R) : h->md;
     const int64_t work =
-        (int64_t)h->md.strips * ((h->md.row_blocks + h->md.item_stride - 1) / h->md.item_stride);
+        (int64_t)base.strips * ((base.row_blocks + base.item_stride - 1) / base.item_stride);
     if (h->mode == MM_FMM_IRS) {
-      LCH(launch_shoot_irs(h->md, work, h->md.square_cells != 0, h->counter.p, h->err.p, st));
+      LCH(launch_shoot_irs(base, work, base.square_cells != 0, h->counter.p, h->err.p, st));
       h->last_segments = 0;
       CKS(record(h, 5, st));
       CKS(record(h, 3, st));
@@ -848,7 +877,8 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
       h->ran = true;
       return MM_OK;
     }
-    const int64_t nseg = std::max<int64_t>(1, std::min(h->segments, work));
+    const int64_t segs = rect ? segments_for(h, (R.r1 - R.r0) * (R.c1 - R.c0)) : h->segments;
+    const int64_t nseg = std::max<int64_t>(1, std::min(segs, work));
     const int64_t per = (work + nseg - 1) / nseg;
     int64_t k = 0;
     for (int64_t w0 = 0; w0 < work; w0 += per, k++) {
@@ -856,9 +886,9 @@ static mm_status run_one(mm_map *h, cudaStream_t st) {
         CK(cudaMemsetAsync(h->counter.p, 0, sizeof(unsigned long long), st));
         CK(cudaMemsetAsync(h->bigq_n.p, 0, 2 * sizeof(unsigned long long), st));
       }
-      MapDev ms = h->md;
+      MapDev ms = base;
       ms.work_begin = -w0;  // this launch's item w is item w0 + w of the map
-      LCH(launch_shoot_ipm(h->d_md.p, &ms, 1, std::min(per, work - w0), h->md.square_cells != 0,
+      LCH(launch_shoot_ipm(h->d_md.p, &ms, 1, std::min(per, work - w0), base.square_cells != 0,
                           h->counter.p, h->err.p, shoot_grid(), st));
       if (h->opt.time_stages) CK(cudaEventRecord(h->seg_ev[2 * k], st));
       LCH(launch_big_ipm(ms, st));
@@ -960,13 +990,31 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
   const double gx0 = P.x0[0], gx1 = P.x0[0] + (double)(P.n[0] - 1) * P.h[0];
   const double gy0 = P.x0[1], gy1 = P.x0[1] + (double)(P.n[1] - 1) * P.h[1];
   const bool explicit_region = h->opt.img_half[0] > 0.0 && h->opt.img_half[1] > 0.0;
+  const bool rect_region = h->opt.star_rect[0] != 0.0 || h->opt.star_rect[1] != 0.0;
   if (P.kappa_star > 0.0 && !explicit_region &&
       (gx0 < bx0 || gx1 > bx1 || gy0 < by0 || gy1 > by1))
     return fail(MM_EINVAL,
                 "the stars' bounding box [%g, %g] x [%g, %g] does not cover the shooting "
                 "region [%g, %g] x [%g, %g]",
                 bx0, bx1, by0, by1, gx0, gx1, gy0, gy1);
-  if (h->opt.star_rect[0] != 0.0 || h->opt.star_rect[1] != 0.0) {
+  if (P.kappa_star > 0.0 && !explicit_region && !rect_region) {
+    // Sec. 3.1: the circular sheet deflects by -kappa_star z only inside the
+    // disk the stars fill (radius max |z_i| about the origin); every ray must
+    // lie inside it, so each corner of the ray grid must
+    double r2 = 0.0;
+    for (int64_t i = 0; i < n_stars; i++)
+      r2 = std::max(r2, pos_xy[2 * i] * pos_xy[2 * i] + pos_xy[2 * i + 1] * pos_xy[2 * i + 1]);
+    const double cx[2] = {gx0, gx1}, cy[2] = {gy0, gy1};
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++)
+        if (cx[a] * cx[a] + cy[b] * cy[b] > r2)
+          return fail(MM_EINVAL,
+                      "ray-grid corner (%g, %g) lies outside the star disk (radius max |z_i| "
+                      "= %g about the origin), where the circular sheet of Sec. 3.1 no "
+                      "longer deflects by -kappa_star z: use a larger star disk",
+                      cx[a], cy[b], std::sqrt(r2));
+  }
+  if (rect_region) {
     // App. B: rectangular star region centred on the origin
     const double c1 = h->opt.star_rect[0], c2 = h->opt.star_rect[1];
     if (!(c1 > 0.0 && c2 > 0.0 && std::isfinite(c1) && std::isfinite(c2)))
@@ -1272,6 +1320,33 @@ mm_status mm_run(mm_map *h, void *stream) {
   if (h->timed_out) return fail(MM_ESTATE, "a previous run timed out");
   CK(cudaSetDevice(h->device));
   return run_one(h, (cudaStream_t)stream);
+}
+
+mm_status mm_run_cells(mm_map *h, int64_t row_begin, int64_t row_end, int64_t col_begin,
+                       int64_t col_end, void *stream) {
+  if (!h) return fail(MM_EINVAL, "handle is NULL");
+  if (h->timed_out) return fail(MM_ESTATE, "a previous run timed out");
+  if (row_begin < h->row_lo || row_end <= row_begin || row_end > h->row_hi ||
+      col_begin < h->col_lo || col_end <= col_begin || col_end > h->col_hi)
+    return fail(MM_EINVAL,
+                "cell rectangle rows [%lld, %lld) x columns [%lld, %lld) is empty or outside "
+                "the handle's rows [%lld, %lld) x columns [%lld, %lld)",
+                (long long)row_begin, (long long)row_end, (long long)col_begin,
+                (long long)col_end, (long long)h->row_lo, (long long)h->row_hi,
+                (long long)h->col_lo, (long long)h->col_hi);
+  CK(cudaSetDevice(h->device));
+  const CellRect r = {row_begin, row_end, col_begin, col_end};
+  return run_one(h, (cudaStream_t)stream, &r);
+}
+
+mm_status mm_normalize_fixed(const mm_map *hc, const uint64_t *acc, float *out, void *stream) {
+  const mm_map *h = hc;
+  if (!h || !acc || !out) return fail(MM_EINVAL, "NULL argument");
+  CK(cudaSetDevice(h->device));
+  CK(launch_scale_fixed(reinterpret_cast<const unsigned long long *>(acc),
+                        (int64_t)h->P.npix * h->P.npix_y, map_scale(h), out,
+                        (cudaStream_t)stream));
+  return MM_OK;
 }
 
 mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {

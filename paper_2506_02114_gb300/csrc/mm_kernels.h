@@ -102,6 +102,10 @@ cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n
                              cudaStream_t st);
 cudaError_t launch_normalize(const unsigned long long *acc, const unsigned long long *span,
                              int npix, int npix_y, double scale, float *out, cudaStream_t st);
+// out[k] = acc[k] * scale for n fixed-point values (the normalisation of an
+// accumulator already folded with its row-difference array)
+cudaError_t launch_scale_fixed(const unsigned long long *acc, int64_t n, double scale,
+                               float *out, cudaStream_t st);
 cudaError_t launch_fold_span(unsigned long long *acc, const unsigned long long *span, int npix,
                              int npix_y,
                              unsigned long long *out, cudaStream_t st);

@@ -7,7 +7,8 @@
 // this library holds that array until the process exits.  Host code must not
 // use g_scratch's name as a device address (on the host it is only a
 // stand-in): its device address is looked up with cudaGetSymbolAddress once
-// per device, with that device current, and cached.
+// per device, with that device current, and cached for the life of the
+// process (a cudaDeviceReset on that device invalidates it).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -67,6 +68,18 @@ __global__ void k_split_stars(const double *__restrict__ pos, const double *__re
 
 __global__ void k_write_mapdev(MapDev md, MapDev *out) { *out = md; }
 
+// Whether p is device (or managed) memory that device `dev` can address as
+// its own; a host pointer or another device's buffer would fault in a kernel.
+bool on_device(const void *p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the (non-sticky) error an unknown pointer leaves
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" mm_status mm_map_plain_fp64_noalloc(
@@ -105,6 +118,16 @@ extern "C" mm_status mm_map_plain_fp64_noalloc(
     }
     base = g_addr[dev];
   }
+  // every pointer the kernels touch must be this device's memory: reject
+  // anything else before any work is enqueued
+  if (n_stars > 0 && (!on_device(masses, dev) || !on_device(pos_xy, dev)))
+    return fail(MM_EINVAL, "masses and pos_xy must be device memory of the current device");
+  if (!on_device(map_out, dev))
+    return fail(MM_EINVAL, "map_out must be device memory of the current device");
+  int sms = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return fail(MM_ECUDA, "cudaDeviceGetAttribute(multiprocessor count)", e);
+  sms = sms > 0 ? sms : 1;
   double *sx = reinterpret_cast<double *>(base + kOffSx);
   double *sy = reinterpret_cast<double *>(base + kOffSy);
   double *sm = reinterpret_cast<double *>(base + kOffSm);
@@ -169,13 +192,26 @@ extern "C" mm_status mm_map_plain_fp64_noalloc(
   if ((e = launch_direct64_vertices(sx, sy, sm, n_stars, C, 0, n0, 0, n1 - 1, verts, st)) !=
       cudaSuccess)
     return fail(MM_ECUDA, "direct-sum deflection", e);
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if ((e = launch_ipm_vertices(d_md, verts, n0, 0, n1 - 1, counter, err, 2 * sms, st)) !=
       cudaSuccess)
     return fail(MM_ECUDA, "inverse polygon mapping", e);
   const double scale = std::ldexp(0.5 * C.hx * C.hy / (delta * delta), -32);
   if ((e = launch_normalize(acc, span, npix, npix, scale, map_out, st)) != cudaSuccess)
     return fail(MM_ECUDA, "normalisation", e);
+  // the kernels' error word (an index check of the MM_DEBUG build): the copy
+  // to pageable host memory returns once the stream has reached it
+  unsigned err_word = 0;
+  if ((e = cudaMemcpyAsync(&err_word, err, sizeof err_word, cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(MM_ECUDA, "reading the error word", e);
+  if (err_word != 0) {
+    char msg[160];
+    snprintf(msg, sizeof msg,
+             "the map kernels reported error bits 0x%x (8: a map index out of range, access "
+             "skipped); map_out is not valid",
+             err_word);
+    return fail(MM_ECUDA, msg);
+  }
   return MM_OK;
 }

@@ -12,6 +12,8 @@
 // The lens equation (Sec. 2.2, circular sheet of Sec. 3.1) then gives
 //   w - W_c = (1-kappa+kappa_*) d + gamma conj(d) - alpha_near
 //             - conj(sum_{l>=2} l c_l zeta^(l-1) / L),   d = z - z_c.
+#include <algorithm>
+
 #include "ipm.cuh"
 #include "mm_kernels.h"
 
@@ -501,6 +503,16 @@ __global__ void __launch_bounds__(256) k_normalize(const unsigned long long *__r
   }
 }
 
+// mu = acc * scale for an accumulator already folded with its difference
+// array (the same arithmetic as k_normalize, so a folded map normalises to
+// the same floats)
+__global__ void __launch_bounds__(256) k_scale_fixed(const unsigned long long *__restrict__ acc,
+                                                     int64_t n, double scale, float *out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = (float)((double)acc[k] * scale);
+}
+
 // acc += row-prefix(span): folds the difference array into the accumulator so
 // the raw fixed-point map can be read back.
 __global__ void k_fold_span(unsigned long long *acc, const unsigned long long *span, int npix,
@@ -643,6 +655,17 @@ cudaError_t launch_big_ipm(const MapDev &m, cudaStream_t st) {
 cudaError_t launch_normalize(const unsigned long long *acc, const unsigned long long *span,
                              int npix, int npix_y, double scale, float *out, cudaStream_t st) {
   k_normalize<<<npix_y, 256, 0, st>>>(acc, span, npix, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_fixed(const unsigned long long *acc, int64_t n, double scale,
+                               float *out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)std::max(sms, 1) * 8);
+  k_scale_fixed<<<(unsigned)blocks, 256, 0, st>>>(acc, n, scale, out);
   return cudaGetLastError();
 }
 

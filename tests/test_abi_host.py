@@ -89,6 +89,37 @@ def test_create_rejects_uncovered_region():
     assert e.value.status == mm.MM_EINVAL and "cover" in str(e.value)
 
 
+def test_create_rejects_grid_outside_the_star_disk():
+    """A ray grid inside the stars' bounding box but with corners outside the
+    disk they fill (radius max |z_i|): the circular sheet's interior form
+    -kappa_star z (Sec. 3.1) would not hold there, so mm_create refuses it
+    before touching a GPU.  A disk reaching past the corners is accepted as
+    far as the host checks go."""
+    kappa, gamma, s, hl, npix, rpp = 0.5, 0.05, 0.0, 3.0, 16, 1.0
+    p = mm.derive_params(kappa, gamma, s, np.ones(4), hl, npix, rpp)
+    X = abs(p.x0[0])
+    Y = abs(p.x0[1])
+    corner = np.hypot(X, Y)
+    R = 1.02 * max(X, Y)
+    assert R < 0.98 * corner        # the box is covered, the corners are not
+    m, pos = synthetic.star_field(4, 4000, R)
+    # the stars reach past the box on all four sides
+    assert pos[:, 0].min() < -X and pos[:, 0].max() > X
+    assert pos[:, 1].min() < -Y and pos[:, 1].max() > Y
+    p = mm.derive_params(kappa, gamma, s, m, hl, npix, rpp)
+    assert np.hypot(pos[:, 0], pos[:, 1]).max() < np.hypot(abs(p.x0[0]), abs(p.x0[1]))
+    with pytest.raises(mm.MMError) as e:
+        mm.create(kappa, gamma, s, m, pos, hl, npix, rpp)
+    assert e.value.status == mm.MM_EINVAL and "star disk" in str(e.value)
+    # the same grid under a disk wide enough passes the host checks (with no
+    # GPU the call then fails at the device, not at validation)
+    m2, pos2 = synthetic.star_field(4, 4000, 1.05 * corner)
+    try:
+        mm.create(kappa, gamma, s, m2, pos2, hl, npix, rpp)
+    except mm.MMError as e2:
+        assert e2.status in (mm.MM_ECUDA, mm.MM_ENOMEM), str(e2)
+
+
 def test_no_gpu_fails_loudly():
     import torch
     if torch.cuda.is_available():

@@ -1,7 +1,9 @@
 """Multi-rank host logic on CPU (gloo, world size 2): sharding one map's cell
-rows over ranks and summing the band maps, and the max-over-ranks step time
-that bench.py reports.  The band maps come from the FP64 oracle, so no GPU
-is needed; on GPUs the same bands come from mm_run with row_begin/row_end."""
+rows over ranks and summing the band maps, the integer all-reduce of the
+fixed-point maps that paper_2506_02114_gb300.shard performs, and the
+max-over-ranks step time that bench.py reports.  The band maps here come
+from the FP64 oracle, so no GPU is needed; on GPUs the same bands come from
+mm_run_cells (tests/test_gpu_shard.py runs that path on one device)."""
 import os
 import socket
 
@@ -72,3 +74,44 @@ def test_band_maps_sum_to_the_whole_map(tmp_path, oracle_mod):
     assert tri == st["triangles"] == 2 * n_rows * (p.n[0] - 1)
     np.testing.assert_allclose(summed, full, rtol=1e-12, atol=1e-12)
     assert ms == 15.0
+
+
+def _reduce_main(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_02114_gb300 import shard
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world)
+    acc = torch.from_numpy(_rank_u64(rank).view(np.int64).copy())
+    shard.reduce_fixed(acc)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "u64.npy"), acc.numpy().view(np.uint64))
+    # a float tensor is refused: the maps travel as int64
+    with pytest.raises(mm.MMError):
+        shard.reduce_fixed(acc.double())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _rank_u64(rank):
+    """Rank's fixed-point map: u64 values across the whole range, including
+    ones at and above 2^63 (negative as int64)."""
+    rng = np.random.default_rng(100 + rank)
+    a = rng.integers(0, 2 ** 63, 4096, dtype=np.uint64) * np.uint64(2)
+    a[:8] = np.array([0, 1, 2 ** 32, 2 ** 63 - 1, 2 ** 63, 2 ** 64 - 1, 2 ** 62, 12345],
+                     dtype=np.uint64)
+    return a
+
+
+def test_fixed_point_maps_sum_exactly_over_ranks(tmp_path):
+    """shard.reduce_fixed on two gloo ranks: the int64 all-reduce of u64 bits
+    equals the u64 sum modulo 2^64 exactly (what makes a sharded map
+    bit-identical to one device's)."""
+    import torch.multiprocessing as tmp
+    world = 2
+    tmp.spawn(_reduce_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    got = np.load(tmp_path / "u64.npy")
+    with np.errstate(over="ignore"):
+        want = _rank_u64(0) + _rank_u64(1)
+    assert got.dtype == np.uint64 and np.array_equal(got, want)
