@@ -215,7 +215,9 @@ typedef struct {
                                sort/scan kernels and memsets not counted) */
   /* stage times of the last mm_run in ms (time_stages = 1), else -1;
      ms_shoot = ms_first_pass (deflection and the one-, two- and 2x2-pixel
-     triangles) + ms_second_pass (the queued larger triangles) */
+     triangles) + ms_second_pass (the queued larger triangles).  For the
+     handle that led the last mm_run_batch (hs[0]), ms_first_pass is the
+     batch's one shared first-pass launch over every map. */
   double ms_tree, ms_expansions, ms_shoot, ms_normalize, ms_total;
   double ms_first_pass, ms_second_pass;
   int32_t rows_per_item;    /* rows of cells per work item in use */

@@ -172,6 +172,7 @@ class Workload:
     seed: int = 0
     img_half: Optional[Tuple[float, float]] = None
     ray_grid: Optional[Tuple[int, int]] = None
+    npix_y: int = 0                # rows of square pixels (0: npix, a square map)
     notes: str = ""
     extra: dict = field(default_factory=dict)
 
@@ -207,6 +208,19 @@ def workload(name: str) -> Workload:
         R = math.sqrt(1e6 * mf.mean / 0.1)
         return Workload(name, 0.5, 0.45, 0.8, mf, R, 1000000, 10000, 25.0,
                         rays_per_pixel=4.75, fmm_order=40, seed=1005)
+    if name == "extreme_mu_10000x1000":
+        # Sec. 5's extreme magnification: (1-k+g)^-1 = 1.5, (1-k-g)^-1 = -1000
+        # (mu_macro = -1500), s = 1 - 5e-5, Salpeter 0.1-2 stars, a source
+        # plane of 100 x 10 theta_E as 10000 x 1000 square pixels of 0.01,
+        # ~100 rays landing per pixel; the disk radius is 1.1 x the shooting
+        # region's half-diagonal (75.2 x 5110.5 theta_E at f = 1e-3)
+        kappa, gamma, s = 0.66717, 0.33383, 1 - 5e-5
+        mf = SALPETER_01_2
+        R = 1.1 * math.hypot(75.2, 5110.5)
+        mu = 1.0 / abs((1 - kappa) ** 2 - gamma ** 2)
+        return Workload(name, kappa, gamma, s, mf, R, n_stars_for((1 - s) * kappa, R, mf),
+                        10000, 50.0, rays_per_pixel=100.0 / mu, fmm_order=25, seed=1006,
+                        npix_y=1000)
     raise KeyError(name)
 
 

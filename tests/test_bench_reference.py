@@ -29,7 +29,7 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["pairs_per_s"] > cb["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"] == "fmm_fp32_salpeter_2000"
+    assert d["config"]["workload"] == "sweep_128" and d["config"]["maps"] == 128
 
 
 def test_reference_arm_other_ranks_exit_without_work():

@@ -1,0 +1,316 @@
+"""Full-size parity of the FMM FP32 path against stored FP64 oracle maps
+(tests/golden/*.npz, written by tests/golden/make_goldens.py from the oracle
+alone), through the C ABI.
+
+* The 2000^2-pixel workload: its downscaled twin (same stars, kappa, gamma,
+  s, p and map extent; 400^2 pixels, ~20 rays landing per pixel) as a whole
+  map; the full-size map's mean against the twin's oracle mean; bands of
+  the full-size run (mm_run_cells on the full-size handle) against the
+  oracle; the full map as the exact sum of its bands.
+* The 5000^2 (5e5 stars, near-critical) and 10000^2 (1e6 stars) workloads:
+  8 tiles of 256 x 256 cells of each full-size plan -- the most near-critical,
+  the most multi-pixel and one across each map edge, chosen from the
+  oracle's deflections -- against the oracle's tile maps, including the
+  pixels hit by near-critical triangles alone, and the oracle's counts of
+  near-critical and multi-pixel triangles.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import paper_2506_02114_gb300 as mm
+import synthetic
+from _metrics import (DEFLECTION_TOL, MAP_P999_TOL, MEAN_TOL, assert_map_parity,
+                      band_errors, deflection_rel_error)
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+TWIN_NPIX = 400
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    mm.lib()
+
+
+def golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.fail("stored oracle values missing: %s (tests/golden/make_goldens.py)" % name)
+    return np.load(path, allow_pickle=False)
+
+
+def same_stars(g, m, pos):
+    return np.allclose(g["star_checksum"], [m.sum(), pos.sum(), (pos * pos).sum()],
+                       rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# the 2000^2-pixel workload
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def full2000(oracle_mod):
+    """The full-size handle of the 2000^2 workload, run once over all cells."""
+    wl = synthetic.workload("fmm_fp32_salpeter_2000")
+    m, pos = wl.stars()
+    p = oracle_mod.derive_params(wl.kappa, wl.gamma, wl.s, m, wl.half_length, wl.npix,
+                                 rays_per_pixel=wl.rays_per_pixel)
+    h = mm.create(wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, wl.npix,
+                  wl.rays_per_pixel, fmm_order=wl.fmm_order)
+    assert mm.get_stats(h)["params"]["n"] == list(p.n)
+    mm.run(h, 0)
+    out = dict(wl=wl, m=m, pos=pos, p=p, h=h, mu=mm.get_map(h).astype(np.float64),
+               fixed=mm.get_map_fixed(h), stats=mm.get_stats(h))
+    yield out
+    mm.destroy(h)
+
+
+def twin_mean_tolerance(g):
+    """Tolerance on |<mu>_full - <mu>_twin| / <mu>_twin.
+
+    Both maps estimate one quantity, the image-plane area of the map's
+    preimage over the map's area; polygon mapping is exact for every cell
+    whose triangles lie inside the map, so the two differ only through the
+    cells straddling the map's edge, whose piecewise-linear images cut the
+    edge slightly differently.  That discretisation error shrinks with the
+    ray spacing h, and the full-size grid's h is 11x finer than the twin's,
+    so the difference is dominated by the twin's own error.  The oracle
+    measured the twin's mean at two ray densities (~5 and ~20 rays landing
+    per pixel, h halving): for an error falling at least like h, the twin's
+    error is at most the difference of the two.  The tolerance is twice that
+    difference, and never below the target's 1e-5."""
+    d = abs(float(g["mean"]) - float(g["mean_coarse"])) / float(g["mean"])
+    return max(MEAN_TOL, 2.0 * d)
+
+
+def test_twin_full_map_against_oracle(oracle_mod, full2000):
+    """The whole twin map (400^2 pixels, ~1.2e7 rays) against the oracle's."""
+    g = golden("twin_fmm_fp32_salpeter_2000.npz")
+    wl, m, pos = full2000["wl"], full2000["m"], full2000["pos"]
+    assert same_stars(g, m, pos)
+    rpp = float(g["rpp"])
+    h = mm.create(wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, TWIN_NPIX, rpp,
+                  fmm_order=wl.fmm_order)
+    st = mm.get_stats(h)
+    assert st["params"]["n"] == [int(x) for x in g["n"]]
+    mm.run(h, 0)
+    mu = mm.get_map(h)
+    st = mm.get_stats(h)
+    mm.destroy(h)
+    p = oracle_mod.derive_params(wl.kappa, wl.gamma, wl.s, m, wl.half_length, TWIN_NPIX,
+                                 rays_per_pixel=rpp)
+    e = assert_map_parity(mu, g["mu"].astype(np.float64), p.mu_macro)
+    assert st["triangles_dropped"] == int(g["dropped"])
+    print("twin: p99.9 %.2e, mean rel %.2e, zero-pixel max %.2e" % (e["p999"], e["mean_rel"],
+                                                                   e["zero_max"]))
+
+
+def test_full_size_mean_against_twin_oracle(full2000):
+    """The full-size run's mean magnification against the twin's oracle mean,
+    within the tolerance derived from the oracle's own two ray densities."""
+    g = golden("twin_fmm_fp32_salpeter_2000.npz")
+    mu = full2000["mu"]
+    assert np.isfinite(mu).all() and (mu >= 0).all()
+    rel = abs(mu.mean() - float(g["mean"])) / float(g["mean"])
+    tol = twin_mean_tolerance(g)
+    print("full-size mean %.9f vs twin oracle %.9f: rel %.2e (tolerance %.2e)"
+          % (mu.mean(), float(g["mean"]), rel, tol))
+    assert rel <= tol
+    st = full2000["stats"]
+    assert st["triangles_dropped"] < 1e-6 * st["cells"]
+
+
+def test_full_size_bands_against_oracle(oracle_mod, full2000):
+    """Bands of full-width cell rows run from the full-size handle's own plan
+    (mm_run_cells: same tree, expansions, culling and queue) against the
+    oracle's band maps: through the centre, near the grid's lower and upper
+    thirds."""
+    p, m, pos, h = full2000["p"], full2000["m"], full2000["pos"], full2000["h"]
+    rows = p.n[1] - 1
+    for r0, nr in ((rows // 2 - 6, 12), (rows // 3, 4), ((2 * rows) // 3 + 17, 4)):
+        mm.run_cells(h, r0, r0 + nr, 0, p.n[0] - 1, 0)
+        mub = mm.get_map(h)
+        ref, _ = oracle_mod.magnification_map(p, m, pos, r0, r0 + nr)
+        assert (ref > 0).sum() > 100
+        e = band_errors(mub, ref, p.mu_macro)
+        print("band rows [%d, %d): p99.9 %.2e, sum rel %.2e" % (r0, r0 + nr, e["p999"],
+                                                              e["mean_rel"]))
+        assert e["p999"] <= MAP_P999_TOL and e["mean_rel"] <= MEAN_TOL, e
+
+
+def test_full_size_map_is_the_sum_of_its_bands(full2000):
+    """Three row bands of the full-size plan add up, in fixed point, to the
+    full run's map bit for bit (what sharding one map over devices relies on)."""
+    p, h = full2000["p"], full2000["h"]
+    rows, cols = p.n[1] - 1, p.n[0] - 1
+    cuts = [0, rows // 3 + 5, (2 * rows) // 3 - 11, rows]
+    tot = np.zeros_like(full2000["fixed"])
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        mm.run_cells(h, a, b, 0, cols, 0)
+        tot += mm.get_map_fixed(h)
+    assert np.array_equal(tot, full2000["fixed"])
+
+
+def test_full_size_deflection_sampled(oracle_mod, full2000):
+    p, m, pos, h = full2000["p"], full2000["m"], full2000["pos"], full2000["h"]
+    rng = np.random.default_rng(2)
+    z = oracle_mod.grid_vertices(p, rng.integers(0, p.n[0], 3000), rng.integers(0, p.n[1], 3000))
+    w = mm.shoot_points(h, z)
+    err = deflection_rel_error(p, z, w, oracle_mod.deflect(p, m, pos, z))
+    assert err.max() <= DEFLECTION_TOL, err.max()
+
+
+# ---------------------------------------------------------------------------
+# the 5000^2 and 10000^2 workloads: tiles of the full-size plans
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["near_critical_5000", "large_kroupa_10000"])
+def test_full_size_tiles_against_oracle(oracle_mod, name):
+    g = golden("tiles_%s.npz" % name)
+    wl = synthetic.workload(name)
+    m, pos = wl.stars()
+    assert same_stars(g, m, pos)
+    p = oracle_mod.derive_params(wl.kappa, wl.gamma, wl.s, m, wl.half_length, wl.npix,
+                                 rays_per_pixel=wl.rays_per_pixel)
+    assert [int(x) for x in g["n"]] == list(p.n)
+    h = mm.create(wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, wl.npix,
+                  wl.rays_per_pixel, fmm_order=wl.fmm_order)
+    try:
+        # the full map once: finite, nothing dropped beyond rays on stars, and
+        # exactly the sum of two halves of its cell rows
+        mm.run(h, 0)
+        full = mm.get_map_fixed(h)
+        st = mm.get_stats(h)
+        assert st["triangles_dropped"] < 1e-6 * st["cells"]
+        rows, cols = p.n[1] - 1, p.n[0] - 1
+        half = rows // 2 + 3
+        mm.run_cells(h, 0, half, 0, cols, 0)
+        tot = mm.get_map_fixed(h)
+        mm.run_cells(h, half, rows, 0, cols, 0)
+        tot += mm.get_map_fixed(h)
+        assert np.array_equal(tot, full)
+        del full, tot
+        T = int(g["tile"])
+        kinds = set()
+        for t in range(int(g["n_tiles"])):
+            r0, c0 = (int(x) for x in g["t%d_origin" % t])
+            kind = str(g["t%d_kind" % t])
+            kinds.add(kind)
+            py0, py1, px0, px1 = (int(x) for x in g["t%d_window" % t])
+            mm.run_cells(h, r0, r0 + T, c0, c0 + T, 0)
+            mu = mm.get_map(h).astype(np.float64)
+            sti = mm.get_stats(h)
+            win = mu[py0:py1, px0:px1]
+            ref = g["t%d_mu" % t].astype(np.float64)
+            # nothing outside the oracle's window
+            outside = mu.sum() - win.sum()
+            assert outside <= 1e-6 * max(float(g["t%d_total" % t]), 1.0), (kind, outside)
+            e = band_errors(win, ref, p.mu_macro) if ref.any() else None
+            crit = g["t%d_crit_mask" % t]
+            ec = band_errors(win[crit], ref[crit], p.mu_macro) if crit.any() else None
+            n_crit, n_multi = int(g["t%d_n_crit" % t]), int(g["t%d_n_multi" % t])
+            print("%s %s tile r%d c%d: p99.9 %s, sum rel %s, near-critical %d/%d "
+                  "(p99.9 on their %d pixels %s), multi-pixel %d/%d"
+                  % (name, kind, r0, c0, e and "%.2e" % e["p999"],
+                     e and "%.2e" % e["mean_rel"], sti["triangles_near_critical"], n_crit,
+                     int(crit.sum()), ec and "%.2e" % ec["p999"], sti["triangles_clipped"],
+                     n_multi))
+            if e is not None:
+                assert e["p999"] <= MAP_P999_TOL and e["mean_rel"] <= MEAN_TOL, (kind, e)
+            if ec is not None:
+                assert ec["p999"] <= MAP_P999_TOL, (kind, ec)
+            # the counts from FP32 vertices against the oracle's FP64 ones
+            # (a triangle right at a threshold or a pixel line may go either way)
+            assert abs(sti["triangles_near_critical"] - n_crit) <= max(3, 0.005 * n_crit)
+            assert abs(sti["triangles_clipped"] - n_multi) <= max(3, 0.005 * n_multi)
+            assert sti["triangles_dropped"] == int(g["t%d_dropped" % t])
+        assert {"near_critical", "multi_pixel", "edge_left", "edge_right", "edge_bottom",
+                "edge_top"} <= kinds
+        # sampled deflections over the tiles' grid region
+        rng = np.random.default_rng(5)
+        k = rng.integers(0, int(g["n_tiles"]), 400)
+        org = np.array([g["t%d_origin" % int(t)] for t in k])
+        i = org[:, 1] + rng.integers(0, T + 1, 400)
+        j = org[:, 0] + rng.integers(0, T + 1, 400)
+        z = oracle_mod.grid_vertices(p, i, j)
+        w = mm.shoot_points(h, z)
+        err = deflection_rel_error(p, z, w, oracle_mod.deflect(p, m, pos, z))
+        assert err.max() <= DEFLECTION_TOL, err.max()
+    finally:
+        mm.destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 5's extreme magnification at the paper's source-plane geometry
+# ---------------------------------------------------------------------------
+
+def test_extreme_magnification_full_geometry(oracle_mod):
+    """Sec. 5's case (mu_macro = -1500, s = 1 - 5e-5, Salpeter 0.1-2 stars)
+    over the paper's 100 x 10 theta_E source plane, as 10000 x 1000 square
+    pixels of 0.01 theta_E with ~100 rays landing per pixel (a 3884 x 264771
+    ray grid 5127 theta_E high).  The FP32 map of the full-size run against
+    the plain FP64 path on the same GPU over three bands of its cell rows
+    (mm_run_cells on the timed handle), against the oracle on two tiles, and
+    sampled source positions within 1e-3 pixel of the oracle's."""
+    import time
+    wl = synthetic.workload("extreme_mu_10000x1000")
+    m, pos = wl.stars()
+    p = oracle_mod.derive_params(wl.kappa, wl.gamma, wl.s, m, wl.half_length, wl.npix,
+                                 rays_per_pixel=wl.rays_per_pixel, npix_y=wl.npix_y)
+    assert abs(p.mu_macro + 1500.0) < 0.1
+    args = (wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, wl.npix, wl.rays_per_pixel)
+    h = mm.create(*args, fmm_order=wl.fmm_order, npix_y=wl.npix_y, time_stages=True)
+    try:
+        st = mm.get_stats(h)
+        assert st["params"]["n"] == list(p.n) and st["params"]["npix_y"] == wl.npix_y
+        import torch
+        t0 = time.perf_counter()
+        mm.run(h, 0)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        mu = mm.get_map(h)
+        st = mm.get_stats(h)
+        assert mu.shape == (wl.npix_y, wl.npix) and np.isfinite(mu).all()
+        print("Sec. 5 geometry: %d stars, %d x %d rays, map %.1f ms on the device (%.2f s wall; "
+              "the paper: ~200 s single, ~600 s double precision on its GPU)"
+              % (len(m), p.n[0], p.n[1], st["ms_total"], wall))
+        rows, cols = p.n[1] - 1, p.n[0] - 1
+        for r0 in (rows // 2 - 150, rows // 3, (3 * rows) // 4):
+            r1 = r0 + 300
+            hp = mm.create(*args, mode=mm.MM_PLAIN_FP64, npix_y=wl.npix_y, row_begin=r0,
+                           row_end=r1)
+            mm.run(hp, 0)
+            ref = mm.get_map(hp).astype(np.float64)
+            mm.destroy(hp)
+            mm.run_cells(h, r0, r1, 0, cols, 0)
+            e = band_errors(mm.get_map(h), ref, p.mu_macro)
+            print("  band [%d, %d) vs plain FP64: p99.9 %.2e, sum rel %.2e"
+                  % (r0, r1, e["p999"], e["mean_rel"]))
+            assert (ref > 0).sum() > 1000
+            assert e["p999"] <= MAP_P999_TOL and e["mean_rel"] <= MEAN_TOL, e
+        for r0, c0 in ((rows // 2 - 128, cols // 2 - 128), (rows // 2 + 40000, cols // 4)):
+            mm.run_cells(h, r0, r0 + 256, c0, c0 + 256, 0)
+            tile = mm.get_map(h)
+            ref, _ = oracle_mod.magnification_map_tile(p, m, pos, r0, r0 + 256, c0, c0 + 256)
+            assert (ref > 0).sum() > 100
+            e = band_errors(tile, ref, p.mu_macro)
+            print("  tile r%d c%d vs oracle: p99.9 %.2e, sum rel %.2e"
+                  % (r0, c0, e["p999"], e["mean_rel"]))
+            assert e["p999"] <= MAP_P999_TOL and e["mean_rel"] <= MEAN_TOL, e
+        # kappa_star = 3.3e-5: positions are held to 1e-3 pixel (the relative
+        # deflection measure's floor sqrt(kappa_star) is a fifth of a pixel)
+        rng = np.random.default_rng(6)
+        z = oracle_mod.grid_vertices(p, rng.integers(0, p.n[0], 4000),
+                                     rng.integers(0, p.n[1], 4000))
+        w = mm.shoot_points(h, z)
+        err_px = np.hypot(*(w - oracle_mod.deflect(p, m, pos, z)).T) / p.delta
+        assert err_px.max() <= 1e-3, err_px.max()
+    finally:
+        mm.destroy(h)

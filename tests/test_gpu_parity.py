@@ -170,48 +170,6 @@ def test_determinism_and_row_bands(oracle_mod):
     assert np.array_equal(tot, a)
 
 
-def test_full_size_fmm_workload_sampled(oracle_mod):
-    """The benchmark workload at full size (1.5e9 rays, 5e4 stars, 2000^2
-    pixels): deflection at sampled grid vertices and the map of a band of
-    cell rows against the oracle, plus invariants of the full map."""
-    wl = synthetic.workload("fmm_fp32_salpeter_2000")
-    m, pos = wl.stars()
-    p = oracle_mod.derive_params(wl.kappa, wl.gamma, wl.s, m, wl.half_length, wl.npix,
-                                 rays_per_pixel=wl.rays_per_pixel)
-    args = (wl.kappa, wl.gamma, wl.s, m, pos, wl.half_length, wl.npix, wl.rays_per_pixel)
-    h = mm.create(*args, fmm_order=wl.fmm_order)
-    st = mm.get_stats(h)
-    assert st["params"]["n"] == list(p.n)
-    mm.run(h, 0)
-    mu = mm.get_map(h)
-    st = mm.get_stats(h)
-    rng = np.random.default_rng(2)
-    i = rng.integers(0, p.n[0], 3000)
-    j = rng.integers(0, p.n[1], 3000)
-    z = oracle_mod.grid_vertices(p, i, j)
-    w = mm.shoot_points(h, z)
-    mm.destroy(h)
-    w_ref = oracle_mod.deflect(p, m, pos, z)
-    err = deflection_rel_error(p, z, w, w_ref)
-    assert err.max() <= DEFLECTION_TOL, err.max()
-    assert np.isfinite(mu).all() and (mu >= 0).all()
-    # one realisation: the mean is |mu_macro| up to the local kappa_* fluctuation
-    assert abs(mu.mean() / abs(p.mu_macro) - 1) < 0.2, mu.mean()
-    assert st["triangles_dropped"] < 1e-6 * st["cells"]
-    # a band of 12 cell rows through the middle of the grid, full width
-    r0 = (p.n[1] - 1) // 2 - 6
-    hb = mm.create(*args, fmm_order=wl.fmm_order, row_begin=r0, row_end=r0 + 12)
-    mm.run(hb, 0)
-    mub = mm.get_map(hb)
-    mm.destroy(hb)
-    mub_ref, _ = oracle_mod.magnification_map(p, m, pos, r0, r0 + 12)
-    assert (mub_ref > 0).sum() > 1000
-    # a band covers most pixels of its footprint only partly (slivers at the
-    # footprint's edge), so the error is measured against max(mu_ref, |mu_macro|)
-    e = band_errors(mub, mub_ref, p.mu_macro)
-    assert e["p999"] <= MAP_P999_TOL and e["mean_rel"] <= MEAN_TOL, e
-
-
 def test_culling_leaves_the_map_unchanged():
     """Culling skips the vertex rows proven (per-sub-cell bounds) to land
     beyond the same map edge as the row below; the cells between such rows
