@@ -484,12 +484,14 @@ def ipm_work(stats):
     return tot
 
 
-def band_rows(st, n_stars, pairs_per_s=4e10, min_rays=1.05e6):
+def band_rows(st, n_stars, pairs_per_s=4e10, min_rays=1.05e6, max_rays=2e7):
     """A band of full-width cell rows through the grid's middle with at least
-    ~1e6 rays, longer where the plain FP64 path takes under ~1 s for it."""
+    ~1e6 rays, longer (up to 2e7 rays) where the plain FP64 path takes under
+    ~1 s for it."""
     n0, n1 = st["params"]["n"]
-    band = int(max(2, min(n1 - 1, max(math.ceil(min_rays / n0),
-                                      pairs_per_s / (n0 * max(n_stars, 1))))))
+    want = max(math.ceil(min_rays / n0), min(pairs_per_s / (n0 * max(n_stars, 1)),
+                                             max_rays / n0))
+    band = int(max(2, min(n1 - 1, want)))
     r0 = (n1 - 1) // 2 - band // 2
     return r0, r0 + band
 

@@ -297,11 +297,14 @@ mm_status mm_run(mm_map *h, void *stream);
 /*
  * Run n handles (all created in MM_FMM_FP32 mode on the current device) with
  * one persistent deflection+mapping launch whose work queue spans every map.
+ * The maps' trees and expansions before it, and their second passes and
+ * normalisation after it, run side by side on up to 8 streams that hs[0]
+ * owns, forked from and joined back to `stream` with events.
  * Asynchronous like mm_run, with no host synchronisation: the batch's
  * descriptor array is assembled on the device (hs[0] holds it), so the call
  * can be captured in a CUDA graph once an earlier call with at least n
- * handles led by hs[0] has sized that array.  Each map is bit-identical to
- * its own mm_run.
+ * handles led by hs[0] has sized that array and created those streams.
+ * Each map is bit-identical to its own mm_run.
  */
 mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream);
 

@@ -30,6 +30,8 @@
 #ifndef MM_SHOOT_MINB
 #define MM_SHOOT_MINB 2
 #endif
+// streams a batch's per-map trees, expansions and second passes run on
+#define MM_BATCH_STREAMS 8
 
 using namespace mm;
 
@@ -246,6 +248,14 @@ struct mm_map {
   // around the batch's one shared deflection + mapping launch
   bool led_batch = false;
   cudaEvent_t batch_ev[2] = {nullptr, nullptr};
+
+  // streams on which this handle, leading an mm_run_batch, runs the maps'
+  // trees and expansions and their second passes side by side (each map's
+  // launches are small; one stream would run them one after another), with
+  // the events that fork them from and join them to the caller's stream
+  std::vector<cudaStream_t> fan;
+  std::vector<cudaEvent_t> fan_join;
+  cudaEvent_t fan_fork[2] = {nullptr, nullptr};
 
   // pinned host scratch for the plan's small reads and uploads: [0, 4) read
   // slots, [8, 8 + MM_DMAX + 2) the level offsets (pageable copies of a few
@@ -1366,26 +1376,47 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
   }
   CK(cudaSetDevice(hs[0]->device));
   mm_map *lead = hs[0];
+  // the lead's fan-out streams (created by its first batch call)
+  const int nfan = std::min<int>(n, MM_BATCH_STREAMS);
+  while ((int)lead->fan.size() < nfan) {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t e2 = nullptr;
+    CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    lead->fan.push_back(s2);
+    CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+    lead->fan_join.push_back(e2);
+  }
+  for (auto &e : lead->fan_fork)
+    if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // fork: the fan streams start after the work the caller queued before
+  CK(cudaEventRecord(lead->fan_fork[0], st));
+  for (int k = 0; k < nfan; k++) CK(cudaStreamWaitEvent(lead->fan[k], lead->fan_fork[0], 0));
   std::vector<const MapDev *> src(n);
   std::vector<int64_t> wb(n);
   int64_t work = 0;
   bool all_square = true;
   for (int i = 0; i < n; i++) {
     mm_map *h = hs[i];
+    cudaStream_t si = lead->fan[i % nfan];
     h->launches = 0;
-    CKS(record(h, 0, st));
-    CKS(clear_map(h, st));
+    CKS(record(h, 0, si));
+    CKS(clear_map(h, si));
     if (h->fresh) {
       h->fresh = false;
-      CKS(record(h, 1, st));
+      CKS(record(h, 1, si));
     } else {
-      CKS(prepare(h, st));
+      CKS(prepare(h, si));
     }
-    CKS(record(h, 2, st));
+    CKS(record(h, 2, si));
     src[i] = h->d_md.p;
     wb[i] = work;
     work += (int64_t)h->md.strips * h->md.row_blocks;
     all_square = all_square && h->md.square_cells;
+  }
+  // join: the shared launch waits for every map's tree and expansions
+  for (int k = 0; k < nfan; k++) {
+    CK(cudaEventRecord(lead->fan_join[k], lead->fan[k]));
+    CK(cudaStreamWaitEvent(st, lead->fan_join[k], 0));
   }
   // the descriptor array is assembled on the device from the handles' own
   // copies: no host staging and no synchronisation, so the whole batch can
@@ -1407,17 +1438,25 @@ mm_status mm_run_batch(mm_map *const *hs, int32_t n, void *stream) {
     CK(cudaEventRecord(lead->batch_ev[1], st));
     lead->led_batch = true;
   }
+  // second passes and normalisation, fanned out again and joined back
+  CK(cudaEventRecord(lead->fan_fork[1], st));
+  for (int k = 0; k < nfan; k++) CK(cudaStreamWaitEvent(lead->fan[k], lead->fan_fork[1], 0));
   for (int i = 0; i < n; i++) {
     mm_map *h = hs[i];
+    cudaStream_t si = lead->fan[i % nfan];
     h->last_segments = 0;  // one first pass for the whole batch
-    CKS(record(h, 5, st));
-    LCH(launch_big_ipm(h->md, st));
-    CKS(record(h, 3, st));
-    LCH(launch_normalize(h->acc.p, h->span.p, h->P.npix, h->P.npix_y, map_scale(h), h->map.p, st));
-    CKS(record(h, 4, st));
+    CKS(record(h, 5, si));
+    LCH(launch_big_ipm(h->md, si));
+    CKS(record(h, 3, si));
+    LCH(launch_normalize(h->acc.p, h->span.p, h->P.npix, h->P.npix_y, map_scale(h), h->map.p, si));
+    CKS(record(h, 4, si));
     h->ev_recorded = h->opt.time_stages != 0;
     h->last_stream = st;
     h->ran = true;
+  }
+  for (int k = 0; k < nfan; k++) {
+    CK(cudaEventRecord(lead->fan_join[k], lead->fan[k]));
+    CK(cudaStreamWaitEvent(st, lead->fan_join[k], 0));
   }
   return MM_OK;
 }
@@ -1657,6 +1696,13 @@ void mm_destroy(mm_map *h) {
   for (auto &e : h->seg_ev)
     if (e) cudaEventDestroy(e);
   for (auto &e : h->batch_ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t f : h->fan) {
+    cudaStreamSynchronize(f);
+    cudaStreamDestroy(f);
+  }
+  for (cudaEvent_t e : h->fan_join) cudaEventDestroy(e);
+  for (auto &e : h->fan_fork)
     if (e) cudaEventDestroy(e);
   if (h->plan_stream) {
     cudaStreamSynchronize(h->plan_stream);
