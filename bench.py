@@ -391,9 +391,10 @@ def measure_peaks(mm, local):
     (mm_measure_peak), with the clocks seen while they ran."""
     out = {}
     with ClockSampler(local) as clk:
-        for kind, key in ((mm.MM_PEAK_FP32_FMA, "fp32_tflops"), (mm.MM_PEAK_FP64_FMA,
-                                                                  "fp64_tflops"),
-                          (mm.MM_PEAK_L2_RED_U64, "l2_red_gops")):
+        for kind, key in ((mm.MM_PEAK_FP32_FMA, "fp32_tflops"),
+                          (mm.MM_PEAK_FP64_FMA, "fp64_tflops"),
+                          (mm.MM_PEAK_L2_RED_U64, "l2_red_gops"),
+                          (mm.MM_PEAK_L2_RED_U64_ROWS, "l2_red_rows_gops")):
             v, ms = mm.measure_peak(kind)
             out[key] = v
             out[key + "_ms"] = ms
@@ -702,9 +703,18 @@ def run_native(args):
         picks = sorted({order[0], order[len(order) // 2], order[-1]})
         pps, bands, worst = plain_and_error(mm, specs, hs, stats, stream, picks)
         ppr = pairs_per_ray(specs, [st["rays"] for st in stats])
+        # the direct sum's inner loop issues 11 FP64 instructions per star-ray
+        # pair (2 subtractions, a multiply and an FMA for |d|^2, the two
+        # Newton-Raphson steps of the reciprocal (4 FMA), the mass multiply and
+        # 2 FMA into the sum): its FP64-pipe load against the FMA-chain probe's
+        # instruction rate (peak TFLOP/s / 2 flops per FMA)
+        dp_rate = 11.0 * pps
+        dp_peak = peaks["fp64_tflops"] * 1e12 / 2.0
         fp64_plain = {"value": pps / ppr, "unit": UNIT, "pairs_per_s": pps,
                       "pairs_per_ray": ppr, "bands": bands,
-                      "speedup_fmm_fp32": value / world / (pps / ppr)}
+                      "speedup_fmm_fp32": value / world / (pps / ppr),
+                      "fp64_pipe": {"dp_inst_per_pair": 11, "achieved_ginst_s": dp_rate / 1e9,
+                                    "probe_ginst_s": dp_peak / 1e9, "frac": dp_rate / dp_peak}}
         map_error = {"p999": worst[0], "mean_rel": worst[1], "tol_p999": MAP_P999_TOL,
                      "tol_mean": MEAN_TOL,
                      "met": worst[0] <= MAP_P999_TOL and worst[1] <= MEAN_TOL,

@@ -424,13 +424,17 @@ mm_status mm_map_plain_fp64_noalloc(double kappa_tot, double shear, double smoot
  *                      a 32 MiB array (L2-resident) with an atomic add whose
  *                      result is unused, the form of the map's fixed-point
  *                      accumulation; *value in 1e9 reductions per second.
+ *   MM_PEAK_L2_RED_U64_ROWS: the same, but a warp's 32 lanes add to 32
+ *                      consecutive words at a scattered position (a pixel
+ *                      row's pixels dealt across a warp).
  * ms (may be NULL) receives the timed launch's duration.  The call allocates
  * (and frees) its 32 MiB array with cudaMalloc.
  */
 typedef enum {
   MM_PEAK_FP32_FMA = 0,
   MM_PEAK_FP64_FMA = 1,
-  MM_PEAK_L2_RED_U64 = 2
+  MM_PEAK_L2_RED_U64 = 2,
+  MM_PEAK_L2_RED_U64_ROWS = 3
 } mm_peak_kind;
 
 mm_status mm_measure_peak(int32_t kind, double *value, double *ms, void *stream);

@@ -98,7 +98,7 @@ EXPORTS = ["mm_derive_params", "mm_create", "mm_run", "mm_run_cells", "mm_run_ba
            "mm_get_stats", "mm_map_plain_fp64_noalloc", "mm_measure_peak", "mm_last_error",
            "mm_destroy"]
 
-MM_PEAK_FP32_FMA, MM_PEAK_FP64_FMA, MM_PEAK_L2_RED_U64 = 0, 1, 2
+MM_PEAK_FP32_FMA, MM_PEAK_FP64_FMA, MM_PEAK_L2_RED_U64, MM_PEAK_L2_RED_U64_ROWS = 0, 1, 2, 3
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)

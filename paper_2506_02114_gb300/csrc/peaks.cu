@@ -6,7 +6,8 @@
 //   FP64 FMA : the same chains in double;
 //   L2 RED   : every thread adds 1 to scattered u64 words of a 32 MiB array
 //              (L2-resident on GB300) with atomicAdd whose result is unused
-//              (a reduction, as the map's fixed-point accumulation issues).
+//              (a reduction, as the map's fixed-point accumulation issues);
+//              "rows": a warp's 32 lanes add to 32 consecutive words.
 //
 // Each kind: one warm-up launch, then the best of three launches timed with
 // CUDA events on `stream`.
@@ -52,6 +53,21 @@ __global__ void __launch_bounds__(256) k_red_u64(unsigned long long *a, uint32_t
   }
 }
 
+// each warp adds 1 to 32 consecutive words (8 sectors of one 256-byte
+// span) at a scattered, warp-uniform position: the pattern of a pixel row's
+// partially covered pixels dealt across a warp's lanes
+__global__ void __launch_bounds__(256) k_red_u64_rows(unsigned long long *a, uint32_t mask,
+                                                      int iters) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t x = (t >> 5) * 0x9E3779B9u + 0x7F4A7C15u;
+  for (int it = 0; it < iters; it++) {
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    atomicAdd(a + (((x << 5) + (t & 31u)) & mask), 1ull);
+  }
+}
+
 mm_status fail(mm_status s, const char *what, cudaError_t e) {
   char buf[256];
   snprintf(buf, sizeof buf, "mm_measure_peak: %s: %s", what, cudaGetErrorString(e));
@@ -67,7 +83,7 @@ extern "C" mm_status mm_measure_peak(int32_t kind, double *value, double *ms_out
     mm::set_last_error("mm_measure_peak: value is NULL");
     return MM_EINVAL;
   }
-  if (kind < MM_PEAK_FP32_FMA || kind > MM_PEAK_L2_RED_U64) {
+  if (kind < MM_PEAK_FP32_FMA || kind > MM_PEAK_L2_RED_U64_ROWS) {
     mm::set_last_error("mm_measure_peak: unknown kind");
     return MM_EINVAL;
   }
@@ -79,7 +95,8 @@ extern "C" mm_status mm_measure_peak(int32_t kind, double *value, double *ms_out
   sms = std::max(sms, 1);
   void *buf = nullptr;
   const size_t words = size_t(1) << 22;  // 32 MiB of u64
-  e = cudaMalloc(&buf, kind == MM_PEAK_L2_RED_U64 ? words * 8 : 64);
+  const bool l2 = kind == MM_PEAK_L2_RED_U64 || kind == MM_PEAK_L2_RED_U64_ROWS;
+  e = cudaMalloc(&buf, l2 ? words * 8 : 64);
   if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA,
                                     "cudaMalloc", e);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -115,9 +132,12 @@ extern "C" mm_status mm_measure_peak(int32_t kind, double *value, double *ms_out
         k_fma_chains<float><<<blocks, threads, 0, st>>>(iters, 0.999999f, 1e-6f, (float *)buf);
       else if (kind == MM_PEAK_FP64_FMA)
         k_fma_chains<double><<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-6, (double *)buf);
-      else
+      else if (kind == MM_PEAK_L2_RED_U64)
         k_red_u64<<<blocks, threads, 0, st>>>((unsigned long long *)buf, (uint32_t)(words - 1),
                                               iters);
+      else
+        k_red_u64_rows<<<blocks, threads, 0, st>>>((unsigned long long *)buf,
+                                                   (uint32_t)(words - 1), iters);
       if ((e = cudaGetLastError()) != cudaSuccess ||
           (e = cudaEventRecord(e1, st)) != cudaSuccess ||
           (e = cudaEventSynchronize(e1)) != cudaSuccess) {
@@ -137,8 +157,7 @@ extern "C" mm_status mm_measure_peak(int32_t kind, double *value, double *ms_out
   cudaFree(buf);
   if (status != MM_OK) return status;
   // TFLOP/s for the FMA kinds, G reductions/s for the L2 kind
-  *value = kind == MM_PEAK_L2_RED_U64 ? work / (best_ms * 1e-3) / 1e9
-                                      : work / (best_ms * 1e-3) / 1e12;
+  *value = l2 ? work / (best_ms * 1e-3) / 1e9 : work / (best_ms * 1e-3) / 1e12;
   if (ms_out) *ms_out = best_ms;
   return MM_OK;
 }
