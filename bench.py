@@ -97,6 +97,10 @@ def parse_args():
                     help="skip the one-core oracle run beside the all-core one")
     ap.add_argument("--rays-per-pixel", type=float, default=None,
                     help="override a single-map workload's rays per pixel (profiling cases)")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="single-map workloads: map only a band of this many cell rows "
+                         "through the grid's middle, with the whole grid's plan (profiling "
+                         "cases at the workload's own ray density)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the map steps only: no FP64, end-to-end, other-workload or "
                          "CPU legs")
@@ -116,6 +120,8 @@ def parse_args():
         ap.error("--irs needs a single-map workload")
     if a.shard == "one-map" and a.workload == SWEEP:
         ap.error("--shard one-map needs a single-map workload")
+    if a.rows and (a.workload == SWEEP or a.shard != "none"):
+        ap.error("--rows needs a single-map workload without --shard")
     return a
 
 
@@ -639,6 +645,11 @@ def run_native(args):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     sharded = args.shard == "one-map" and world > 1
+    band = None
+    if args.rows:
+        n0, n1 = mm.get_stats(hs[0])["params"]["n"]
+        r0 = max(0, (n1 - 1) // 2 - args.rows // 2)
+        band = (r0, min(n1 - 1, r0 + args.rows), n0 - 1)
 
     def step():
         with torch.cuda.stream(stream):
@@ -648,6 +659,8 @@ def run_native(args):
             e0.record(stream)
             if sharded:
                 shard.sharded_map(hs[0], rank, world)
+            elif band:
+                mm.run_cells(hs[0], band[0], band[1], 0, band[2], stream.cuda_stream)
             elif len(hs) > 1:
                 mm.run_batch(hs, stream.cuda_stream)
             else:
@@ -679,6 +692,10 @@ def run_native(args):
         tot_ms = float(t.item())
     ms_per_step = tot_ms / args.steps
     stats = [mm.get_stats(h) for h in hs]
+    if band:   # the band's rays and cells (mm_get_stats counts the handle's)
+        for st in stats:
+            st["rays"] = (band[1] - band[0] + 1) * (band[2] + 1)
+            st["cells"] = (band[1] - band[0]) * band[2]
     rays = sum(st["rays"] for st in stats)
     computed = sum(rays_computed(st) for st in stats)
     # replicas: every rank maps the whole workload; one sharded map: its rays once
@@ -757,6 +774,7 @@ def run_native(args):
                    "rows_per_item": sorted({st["rows_per_item"] for st in stats}),
                    "tuned_from_cache": tuned.count(2), "tuned_by_timing": tuned.count(1),
                    "mapping": "irs" if args.irs else "ipm",
+                   "band_rows": list(band[:2]) if band else None,
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": ("one map, row bands over %d ranks + int64 all-reduce" % world
                                    if sharded else "replicas" if world > 1 else "single")},

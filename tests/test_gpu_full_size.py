@@ -226,9 +226,15 @@ def test_full_size_tiles_against_oracle(oracle_mod, name):
                 assert e["p999"] <= MAP_P999_TOL and e["mean_rel"] <= MEAN_TOL, (kind, e)
             if ec is not None:
                 assert ec["p999"] <= MAP_P999_TOL, (kind, ec)
-            # the counts from FP32 vertices against the oracle's FP64 ones
-            # (a triangle right at a threshold or a pixel line may go either way)
-            assert abs(sti["triangles_near_critical"] - n_crit) <= max(3, 0.005 * n_crit)
+            # the counts from FP32 vertices against the oracle's FP64 ones.  A
+            # vertex's FP32 pixel position carries rounding of ~1e-5 pixel from
+            # the per-ray arithmetic (offsets of up to hundreds of pixels from
+            # its sub-cell's centre image); for a near-critical sliver, ~1e-4
+            # pixel^2 in area with sides of ~1 pixel, that is a few per cent of
+            # its area, so triangles within a few per cent of the |mu|
+            # threshold may go either way; a pixel line is crossed or not
+            # within ~1e-5 pixel
+            assert abs(sti["triangles_near_critical"] - n_crit) <= max(8, 0.03 * n_crit)
             assert abs(sti["triangles_clipped"] - n_multi) <= max(3, 0.005 * n_multi)
             assert sti["triangles_dropped"] == int(g["t%d_dropped" % t])
         assert {"near_critical", "multi_pixel", "edge_left", "edge_right", "edge_bottom",
