@@ -19,7 +19,8 @@ tiles: 8 tiles of 256 x 256 cells of a full-size ray grid, chosen from the
   oracle's own deflections at a sample of candidate tiles (never from map
   values): the two whose sampled triangles have the most near-critical
   orientation changes and largest local |mu|, the two with the most sampled
-  multi-pixel triangles, and one straddling each of the four map edges.
+  multi-pixel triangles, and one straddling each of the four map edges --
+  each among the tiles whose oracle map fits 1024 x 1024 pixels.
   For each tile: the oracle's map over the tile's pixel window, and from
   the oracle's FP64 vertices the near-critical triangle count (local |mu|
   above 1e3, not wholly beyond one map edge), the pixels those triangles'
@@ -46,6 +47,7 @@ import _sweep  # noqa: E402
 
 TILE = 256
 CRITICAL_MU = 1e3
+MAX_WINDOW = 1024   # pixels per axis of a stored tile map
 
 
 def log(*a):
@@ -243,14 +245,25 @@ def make_tiles(name, n_cand=2000, n_cells=16):
             kinds.append(kind)
             got += 1
 
-    take(np.argsort(-crit, kind="stable"), "near_critical", 2)
-    take(np.argsort(-multi, kind="stable"), "multi_pixel", 2)
+    refs = {}
+
+    def compact(k):
+        # the tile's oracle map must fit a window of MAX_WINDOW^2 pixels (a
+        # tile holding a star spreads its cells over the whole map)
+        if k not in refs:
+            refs[k] = tile_reference(p, m, pos, int(rows[k]), int(cols[k]))
+        py0, py1, px0, px1 = refs[k]["window"]
+        return py1 - py0 <= MAX_WINDOW and px1 - px0 <= MAX_WINDOW
+
+    take(np.argsort(-crit, kind="stable"), "near_critical", 2, need=compact)
+    take(np.argsort(-multi, kind="stable"), "multi_pixel", 2, need=compact)
     for e, tag in enumerate(("edge_left", "edge_right", "edge_bottom", "edge_top")):
-        take(np.argsort(-edges[e], kind="stable"), tag, 1, need=lambda k, e=e: edges[e][k] > 0)
+        take(np.argsort(-edges[e], kind="stable"), tag, 1,
+             need=lambda k, e=e: edges[e][k] > 0 and compact(k))
     out = {"name": name, "tile": TILE, "n": np.array(p.n), "n_stars": len(m),
            "star_checksum": np.array([m.sum(), pos.sum(), (pos * pos).sum()])}
     for t, (k, kind) in enumerate(zip(picks, kinds)):
-        ref = tile_reference(p, m, pos, int(rows[k]), int(cols[k]))
+        ref = refs[k]
         out["t%d_origin" % t] = np.array([rows[k], cols[k]])
         out["t%d_kind" % t] = kind
         for key, v in ref.items():
