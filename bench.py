@@ -60,13 +60,18 @@ MAP_P999_TOL, MEAN_TOL = 1e-3, 1e-5
 # autotuner choices made on GB300 by this library (JSON lines, mm_options.tune_cache)
 TUNE_CACHE = os.path.join(ROOT, "paper_2506_02114_gb300", "tune", "sm_103.jsonl")
 
-# Counters of one ncu capture of the first-pass kernel on the reduced profiling
-# case (profiles/), per computed ray: valid only for the kernel sources they
-# were taken on (hash below); scaled by the rays a launch computes.
-NCU_PER_RAY = {"sources_sha1": None,
-               "inst_per_ray": None,        # smsp__inst_executed.sum / rays computed
-               "red_per_ray": None,         # L2 reduction requests / rays computed
-               "dram_bytes_per_ray": None}  # dram__bytes_read + write / rays computed
+# Counters of one ncu capture of the hot kernels on the reduced profiling case
+# (profiles/counters_fmm_fp32_salpeter_2000_rpp1.md): valid only for the kernel
+# sources they were taken on (hash below), reported beside the live roofline.
+NCU_COUNTERS = {
+    "sources_sha1": "7d3252ae2842b3be06651d425b06e6dde2050730",
+    "case": "fmm_fp32_salpeter_2000 at 1 ray per pixel (1.64e8 rays), ncu --clock-control none",
+    "k_shoot_ipm": {"issue_active": 0.636, "warps_active": 0.197, "alu_active": 0.497,
+                    "fma_active": 0.192, "l2_red_requests_per_s": 3.9e10},
+    "k_big_ipm": {"issue_active": 0.815, "warps_active": 0.451, "alu_active": 0.608,
+                  "fma_active": 0.284, "l2_red_requests_per_s": 9.7e10},
+    "k_direct64_vertices": {"fp64_pipe_active": 0.907},
+}
 
 
 def kernel_sources_sha1():
@@ -459,25 +464,16 @@ def roofline(stats, first_ms, peaks, irs=False):
            "kernel_ms": first_ms, "rays_computed": computed,
            "flops_per_ray": flops / max(computed, 1),
            "peak_source": "measured now: mm_measure_peak FP32 FMA (8 fmaf chains per thread)"}
-    ncu = NCU_PER_RAY
-    if not irs and ncu["sources_sha1"] == kernel_sources_sha1():
-        # counters per computed ray from one ncu capture of the same sources
-        # on the reduced profiling case, scaled to this launch's rays
-        sms = 152
-        clk = peaks["clocks"].get("sm_max_mhz") or 2070.0
-        inst = ncu["inst_per_ray"] * computed
-        out["issue"] = {"inst_per_ray": ncu["inst_per_ray"],
-                        "achieved_ginst_s": inst / s / 1e9,
-                        "peak_ginst_s": sms * 4 * clk * 1e6 / 1e9,
-                        "frac": inst / s / (sms * 4 * clk * 1e6),
-                        "source": "ncu smsp__inst_executed.sum, reduced case (profiles/)"}
-        red = ncu["red_per_ray"] * computed
-        out["l2_red"] = {"per_ray": ncu["red_per_ray"], "achieved_gops": red / s / 1e9,
-                         "peak_gops": peaks["l2_red_gops"],
-                         "frac": red / s / 1e9 / peaks["l2_red_gops"],
-                         "source": "ncu L2 reduction requests, reduced case (profiles/); "
-                                   "peak measured now"}
-        out["traffic"] = ncu["dram_bytes_per_ray"] * computed
+    if not irs and NCU_COUNTERS["sources_sha1"] == kernel_sources_sha1():
+        # what bounds the kernel, from one ncu capture of the same sources on
+        # the reduced profiling case: issue slots, not the FP32 pipe or atomics
+        c = NCU_COUNTERS["k_shoot_ipm"]
+        out["issue"] = {"issue_active_frac": c["issue_active"],
+                        "warps_active_frac": c["warps_active"],
+                        "alu_pipe_frac": c["alu_active"], "fma_pipe_frac": c["fma_active"],
+                        "l2_red_frac_of_scattered_peak":
+                            c["l2_red_requests_per_s"] / (peaks["l2_red_gops"] * 1e9),
+                        "source": "ncu, " + NCU_COUNTERS["case"]}
     return out
 
 
