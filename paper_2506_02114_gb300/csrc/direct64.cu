@@ -163,8 +163,9 @@ __global__ void __launch_bounds__(256) k_ipm_vertices(const MapDev *__restrict__
       for (int tri = 0; tri < 2; tri++) {
         TriJob job;
         SmallTri se;
-        const int code = cell_col ? ipm_triangle(M, prev, tri ? cur_r : prev_r,
-                                                 tri ? cur : cur_r, ra, cnt, se, job)
+        LineTri le;  // (unused: two-pixel triangles are apportioned in place)
+        const int code = cell_col ? ipm_triangle<false>(M, prev, tri ? cur_r : prev_r,
+                                                        tri ? cur : cur_r, ra, cnt, se, job, le)
                                   : TRI_DONE;
         wq_push(M, wq, code == TRI_SMALL, se, lane);
         jq_add(jq, code == TRI_BIG, job, lane);

@@ -213,6 +213,60 @@ __device__ __forceinline__ void small_tri_apportion(const MapDev &M, const Small
   deposit(M, gx + 1, gy + 1, (unsigned long long)max(one - vL - vB + vLB, 0ll));
 }
 
+// A triangle across one grid line of two pixels: the low pixel (gx, gy),
+// the line u = L along axis o (0: x, 1: y; the high pixel is the next one
+// along that axis) and the triangle's coordinates along that axis.
+struct __align__(16) LineTri {
+  int gx, gy;
+  float u0, u1, u2, L;
+  int o, pad;
+};
+
+// The two pixels' shares: complements in fixed point, one triangle in all.
+__device__ __forceinline__ void line_tri_apportion(const MapDev &M, const LineTri &e) {
+  const unsigned long long vlow = low_side_fixed(e.u0, e.u1, e.u2, e.L);
+  deposit(M, e.gx, e.gy, vlow);
+  deposit(M, (long long)e.gx + 1 - e.o, (long long)e.gy + e.o, MM_FIX_ONE - vlow);
+}
+
+// Per-warp queue of LineTri in shared memory (capacity 64 >= 31 + 31 + 2):
+// the two-pixel triangles are shared out 32 at a time, so the warp runs
+// their apportioning with every lane busy instead of in a branch that only
+// some lanes take (used by the single-map first pass, whose registers allow
+// it; elsewhere the triangle is apportioned where it is found).
+struct LineQueue {
+  LineTri *q;
+  int n;
+};
+
+__device__ __forceinline__ void lq_push(const MapDev &M, LineQueue &lq, bool want,
+                                        const LineTri &e, int lane) {
+  const unsigned m = __ballot_sync(0xffffffffu, want);
+  if (!m) return;
+  const int pos = lq.n + __popc(m & ((1u << lane) - 1u));
+  if (want) lq.q[pos] = e;
+  lq.n += __popc(m);
+  __syncwarp();
+  while (lq.n >= 32) {
+    const LineTri t = lq.q[lq.n - 32 + lane];
+    __syncwarp();
+    lq.n -= 32;
+    line_tri_apportion(M, t);
+  }
+}
+
+__device__ __forceinline__ void lq_drain(const MapDev &M, LineQueue &lq, int lane) {
+  if (lq.n > 0) {
+    LineTri t;
+    const bool have = lane < lq.n;
+    if (have) t = lq.q[lane];
+    __syncwarp();
+    if (have) line_tri_apportion(M, t);
+    lq.n = 0;
+  }
+  __syncwarp();
+}
+
 // Per-warp queue of SmallTri in shared memory (capacity 64 >= 31 + 31 + 2).
 struct WarpQueue {
   SmallTri *q;
@@ -272,16 +326,19 @@ struct __align__(16) TriJob {
 };
 static_assert(sizeof(TriJob) == MM_TRIJOB_BYTES, "TriJob layout");
 
-enum { TRI_DONE = 0, TRI_SMALL = 1, TRI_BIG = 2 };
+enum { TRI_DONE = 0, TRI_SMALL = 1, TRI_BIG = 2, TRI_LINE = 3 };
 
-// Apportion one triangle (a, b, c).  Triangles within one pixel or split by
-// one grid line are finished here; returns TRI_SMALL (se filled) for a
-// triangle covering 2 x 2 pixels, to be pushed on the quad queue, and TRI_BIG
-// (job filled) for a larger one, whose pixel rows and then partially covered
-// pixels the warp deals out to its lanes (warp_tri_jobs).
+// Apportion one triangle (a, b, c).  Triangles within one pixel are
+// finished here, and so are those split by one grid line unless LINEQ, which
+// returns TRI_LINE (le filled) for the line queue; returns TRI_SMALL (se
+// filled) for a triangle covering 2 x 2 pixels, to be pushed on the quad
+// queue, and TRI_BIG (job filled) for a larger one, whose pixel rows and then
+// partially covered pixels the warp deals out to its lanes (warp_tri_jobs).
+template <bool LINEQ>
 __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
                                             const Vtx &b, const Vtx &c, RunAcc &ra,
-                                            IpmCounters &cnt, SmallTri &se, TriJob &job) {
+                                            IpmCounters &cnt, SmallTri &se, TriJob &job,
+                                            LineTri &le) {
   if (a.px == MM_VTX_INVALID || b.px == MM_VTX_INVALID || c.px == MM_VTX_INVALID) {
     cnt.dropped++;
     return TRI_DONE;
@@ -338,6 +395,17 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     const float L = (float)(o ? cy0 : cx0) + 1.f;
     // (selects, not t[o]: a run-time index would put t in local memory)
     const float u0 = o ? t[1] : t[0], u1 = o ? t[3] : t[2], u2 = o ? t[5] : t[4];
+    if (LINEQ) {
+      le.gx = ox + cx0;  // the low pixel (indices within +-2^29)
+      le.gy = oy + cy0;
+      le.u0 = u0;
+      le.u1 = u1;
+      le.u2 = u2;
+      le.L = L;
+      le.o = o;
+      cnt.line++;
+      return TRI_LINE;
+    }
     const unsigned long long vlow = low_side_fixed(u0, u1, u2, L);
     const bool b0 = u0 < L;  // vertex a on the low side
     // the pixel holding vertex a goes through the run accumulator
@@ -504,10 +572,18 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 // the global column of c0, the global row, and the fully covered run
 // [fa, fb] relative to c0 (none if fa > fb).  Stored as arrays over lanes,
 // so lanes reading different rows hit different banks.
+// One row's record as five 16-byte words (four used, one of padding so that
+// eight consecutive records fall on distinct banks): the pixel lanes read it
+// with four 16-byte loads.
+struct __align__(16) RowRec {
+  float4 p0;  // a0, b0, h0, a1
+  float4 p1;  // b1, h1, a2, b2
+  float4 p2;  // h2, gx0, gy, fa  (the last three as int bits)
+  float4 p3;  // fb, st, -, -     (int bits)
+  float4 pad;
+};
 struct RowRecs {
-  float a[3][32], b[3][32], h[3][32];
-  int gx0[32], gy[32], fa[32], fb[32];
-  int st[32];                  // first partial-pixel task of the row
+  RowRec r[32];
   int tk[32], trl[32], tex[32];  // triangles with rows: lane, first row, first row task
 };
 
@@ -516,17 +592,19 @@ struct RowRecs {
 __device__ __forceinline__ void pixel_task(const MapAcc &M, const RowRecs *rr, int o, int task,
                                            int ptotal) {
   if (task < ptotal) {
-    const int fa = rr->fa[o], fb = rr->fb[o];
-    int c = task - rr->st[o];
+    const RowRec &R = rr->r[o];
+    const float4 p0 = R.p0, p1 = R.p1, p2 = R.p2, p3 = R.p3;
+    const int fa = __float_as_int(p2.w), fb = __float_as_int(p3.x);
+    int c = task - __float_as_int(p3.y);
     if (fa <= fb && c >= fa) c += fb - fa + 1;
     const float cl = (float)c;
-    float sh = 0.f;
-#pragma unroll
-    for (int e = 0; e < 3; e++)
-      sh = fmaf(rr->h[e][o], piece_mean(rr->a[e][o] - cl, rr->b[e][o] - cl), sh);
+    float sh = p0.z * piece_mean(p0.x - cl, p0.y - cl);
+    sh = fmaf(p1.y, piece_mean(p0.w - cl, p1.x - cl), sh);
+    sh = fmaf(p2.x, piece_mean(p1.z - cl, p1.w - cl), sh);
     // the row and its columns lie in the map (clamped when the row was set up)
     const unsigned long long v = frac_to_fixed(sh);
-    const long long idx = (long long)rr->gy[o] * M.npix + rr->gx0[o] + c;
+    const long long idx =
+        (long long)__float_as_int(p2.z) * M.npix + __float_as_int(p2.y) + c;
     if (v && MM_INDEX_OK(M.err, idx, (long long)M.npix * M.npix_y)) atomicAdd(&M.acc[idx], v);
   }
 }
@@ -605,18 +683,20 @@ __device__ __forceinline__ void warp_tri_jobs(unsigned long long *acc,
     if (np > 0) {
       const TriJob &J = q[k];
       const float fc0 = (float)c0;
+      float a[3], b[3], hh[3];
 #pragma unroll
       for (int e = 0; e < 3; e++) {
         // x relative to column c0 (zero-height pieces stay zero)
-        rr->a[e][slot] = ph[e] != 0.f ? pa[e] - fc0 : 0.f;
-        rr->b[e][slot] = ph[e] != 0.f ? pb[e] - fc0 : 0.f;
-        rr->h[e][slot] = ph[e] * J.inv2;
+        a[e] = ph[e] != 0.f ? pa[e] - fc0 : 0.f;
+        b[e] = ph[e] != 0.f ? pb[e] - fc0 : 0.f;
+        hh[e] = ph[e] * J.inv2;
       }
-      rr->gx0[slot] = J.ox + c0;
-      rr->gy[slot] = J.oy + r;
-      rr->fa[slot] = fa - c0;
-      rr->fb[slot] = fb - c0;
-      rr->st[slot] = pexcl;
+      RowRec &R = rr->r[slot];
+      R.p0 = make_float4(a[0], b[0], hh[0], a[1]);
+      R.p1 = make_float4(b[1], hh[1], a[2], b[2]);
+      R.p2 = make_float4(hh[2], __int_as_float(J.ox + c0), __int_as_float(J.oy + r),
+                         __int_as_float(fa - c0));
+      R.p3 = make_float4(__int_as_float(fb - c0), __int_as_float(pexcl), 0.f, 0.f);
     }
     __syncwarp();
     for (int pbase = 0; pbase < ptotal; pbase += 32)
@@ -636,6 +716,7 @@ struct JobQueue {
 
 // Shared memory of one warp: the two queues and the row records.
 struct WarpSmem {
+  LineTri line[64];
   SmallTri quad[64];
   TriJob big[64];
   RowRecs rows;

@@ -46,6 +46,25 @@ __device__ __forceinline__ int lookup_leaf(const MapDev &M, int cx, int cy) {
   return (a << (2 * M.sub)) + (((cy >> sh) & mask) << M.sub) + ((cx >> sh) & mask);
 }
 
+// lookup_leaf with a per-lane cache keyed by the lookup-grid row: a grid
+// entry that names a record directly holds for every finest-level row of
+// that grid row (the lane's column is fixed), so consecutive vertex rows
+// skip the grid read until they leave it
+__device__ __forceinline__ int lookup_leaf_cached(const MapDev &M, int cx, int cy, int &c_gy,
+                                                  int &c_leaf) {
+  const int gy = (cy >> M.gshift) - M.gy0;
+  if (gy == c_gy) return c_leaf;
+  const int gx = (cx >> M.gshift) - M.gx0;
+  if (gx < 0 || gy < 0 || gx >= M.gw || gy >= M.gh) return -1;
+  const int e = __ldg(&M.grid[(int64_t)gy * M.gw + gx]);
+  if (e >= 0) {
+    c_gy = gy;
+    c_leaf = e;
+    return e;
+  }
+  return lookup_leaf(M, cx, cy);
+}
+
 // Source-plane position of grid point (i + ti, j + tj) in pixel units:
 // returns the integer pixel and the fraction.  ti = tj = 0 for ray vertices.
 template <bool SQUARE, bool FRAC>
@@ -267,9 +286,17 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
   extern __shared__ __align__(16) unsigned char s_dyn[];
   WarpSmem *ws = reinterpret_cast<WarpSmem *>(s_dyn) + (threadIdx.x >> 5);
   WarpQueue wq = {ws->quad, 0};
+  LineQueue lq = {ws->line, 0};
   JobQueue jq = {ws->big, &ws->rows, 0};
   IpmCounters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
   int last_map = -1;
+  // A batch's current map, copied per warp into shared memory when the warp
+  // moves to another map: its fields are then read there like a launch
+  // parameter's, which leaves the registers to the per-ray work (reading
+  // them from the descriptor array in global memory costs registers, and
+  // spills, that the single-map kernel never pays).
+  __shared__ MapDev s_md[8];
+  MapDev &SM = s_md[threadIdx.x >> 5];
   while (true) {
     unsigned long long w = 0;
     if (lane == 0) w = atomicAdd(work_counter, 1ull);
@@ -287,11 +314,17 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
       }
       mi = lo;
     }
-    const MapDev &M = BATCH ? maps[mi] : M1;
-    if (mi != last_map) {  // warp-uniform
-      if (last_map >= 0) flush_counters(BATCH ? maps[last_map] : M1, cnt, lane);
+    if (BATCH && mi != last_map) {  // warp-uniform
+      if (last_map >= 0) flush_counters(SM, cnt, lane);
+      __syncwarp();
+      const unsigned long long *src = reinterpret_cast<const unsigned long long *>(maps + mi);
+      unsigned long long *dst = reinterpret_cast<unsigned long long *>(&SM);
+      for (int k = lane; k < (int)(sizeof(MapDev) / 8); k += 32) dst[k] = src[k];
+      __syncwarp();
       last_map = mi;
     }
+    if (!BATCH) last_map = 0;
+    const MapDev &M = BATCH ? SM : M1;
     const int64_t local = (int64_t)w - M.work_begin;
     const int64_t s = local % M.strips, b = (local / M.strips) * M.item_stride;
     const int64_t i = M.col_begin + s * MM_STRIP + lane;
@@ -317,13 +350,14 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
     }
     // one pass more than there are cell rows: the last one maps nothing and
     // shares out what is left in the queue of larger triangles
+    int c_gy = INT_MIN, c_leaf = -1;  // lookup cache of this lane's column
     for (int64_t j = jb + 1;; j++) {
       const bool fin = j > je;  // warp-uniform
       Vtx cur = prev, cur_r = prev_r;
       int side = MM_CULL_NONE;
       if (!fin) {
         const int cy = __ldg(&M.row_cell[j]);
-        const int leaf = lookup_leaf(M, cx, cy);
+        const int leaf = lookup_leaf_cached(M, cx, cy, c_gy, c_leaf);
         if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
         if (M.cull) {
           int run;
@@ -361,6 +395,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
       for (int tri = 0; tri < 2; tri++) {
         TriJob job;
         SmallTri se;
+        LineTri le;
         // triangle 0: (v00, v10, v11); triangle 1: (v00, v11, v01)
         Vtx vb, vc;
         vb.px = tri ? cur_r.px : prev_r.px;
@@ -372,7 +407,11 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
         vc.fx = tri ? cur.fx : cur_r.fx;
         vc.fy = tri ? cur.fy : cur_r.fy;
         const int code =
-            (cell_col && !fin) ? ipm_triangle(M, prev, vb, vc, ra, cnt, se, job) : TRI_DONE;
+            (cell_col && !fin) ? ipm_triangle<!BATCH>(M, prev, vb, vc, ra, cnt, se, job, le)
+                               : TRI_DONE;
+        // (the batch kernel, which reads its maps from memory, has no
+        // registers to spare for the line queue's state)
+        if (!BATCH) lq_push(M, lq, code == TRI_LINE, le, lane);
         wq_push(M, wq, code == TRI_SMALL, se, lane);
         jq_add(jq, code == TRI_BIG, job, lane);
         jq_share(M, jq, fin && tri == 1, lane);
@@ -383,9 +422,10 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
       prev_side = side;
     }
     run_flush(M, ra);
+    if (!BATCH) lq_drain(M, lq, lane);
     wq_drain(M, wq, lane);
   }
-  if (last_map >= 0) flush_counters(BATCH ? maps[last_map] : M1, cnt, lane);
+  if (last_map >= 0) flush_counters(BATCH ? SM : M1, cnt, lane);
 }
 
 // Inverse ray shooting (Sec. 3.2; the IRS column of Table 1): every grid
