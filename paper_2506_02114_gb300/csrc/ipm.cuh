@@ -85,12 +85,13 @@ __device__ __forceinline__ bool mm_index_ok(unsigned *err, long long idx, long l
 #define MM_INDEX_OK(err, idx, n) true
 #endif
 
-// Add v fixed-point units to map pixel (gx, gy) if it lies in the map.
-__device__ __forceinline__ void deposit(const MapDev &M, long long gx, long long gy,
-                                        unsigned long long v) {
+// Add v fixed-point units to map pixel (gx, gy) if it lies in the map
+// (pixel indices stay within +-2^30: vertices are clamped to +-2^28 pixels
+// about their sub-cell's centre image, and boxes to +-1e9 of a vertex).
+__device__ __forceinline__ void deposit(const MapDev &M, int gx, int gy, unsigned long long v) {
   if (v && gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix_y &&
-      MM_INDEX_OK(M.err, gy * M.npix + gx, (long long)M.npix * M.npix_y))
-    atomicAdd(&M.acc[gy * M.npix + gx], v);
+      MM_INDEX_OK(M.err, (long long)gy * M.npix + gx, (long long)M.npix * M.npix_y))
+    atomicAdd(&M.acc[(long long)gy * M.npix + gx], v);
 }
 
 // The map's accumulators alone, passed as scalars to the out-of-line row
@@ -206,7 +207,7 @@ __device__ __forceinline__ void small_tri_apportion(const MapDev &M, const Small
   const float A2 = e.d1x * e.d2y - e.d2x * e.d1y;  // twice the signed area
   const long long vLB = (long long)frac_to_fixed(2.f * lb * rcp_approx_f(A2));
   const long long one = (long long)MM_FIX_ONE;
-  const long long gx = (long long)e.ox + c0, gy = (long long)e.oy + r0;
+  const int gx = e.ox + c0, gy = e.oy + r0;
   deposit(M, gx, gy, (unsigned long long)vLB);
   deposit(M, gx, gy + 1, (unsigned long long)max(vL - vLB, 0ll));
   deposit(M, gx + 1, gy, (unsigned long long)max(vB - vLB, 0ll));
@@ -226,7 +227,7 @@ struct __align__(16) LineTri {
 __device__ __forceinline__ void line_tri_apportion(const MapDev &M, const LineTri &e) {
   const unsigned long long vlow = low_side_fixed(e.u0, e.u1, e.u2, e.L);
   deposit(M, e.gx, e.gy, vlow);
-  deposit(M, (long long)e.gx + 1 - e.o, (long long)e.gy + e.o, MM_FIX_ONE - vlow);
+  deposit(M, e.gx + 1 - e.o, e.gy + e.o, MM_FIX_ONE - vlow);
 }
 
 // Per-warp queue of LineTri in shared memory (capacity 64 >= 31 + 31 + 2):
@@ -377,9 +378,9 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   const int cy0 = (int)floorf(fmaxf(ymin, -lim)), cy1 = (int)floorf(fminf(ymax, lim));
   if (cx0 == cx1 && cy0 == cy1) {
     // whole triangle inside one pixel
-    const long long gx = (long long)ox + cx0, gy = (long long)oy + cy0;
+    const int gx = ox + cx0, gy = oy + cy0;
     if (gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix_y)
-      run_add(M, ra, gy * M.npix + gx, MM_FIX_ONE);
+      run_add(M, ra, (long long)gy * M.npix + gx, MM_FIX_ONE);
     return TRI_DONE;
   }
   if ((cx1 - cx0) + (cy1 - cy0) == 1) {
@@ -409,21 +410,21 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     const unsigned long long vlow = low_side_fixed(u0, u1, u2, L);
     const bool b0 = u0 < L;  // vertex a on the low side
     // the pixel holding vertex a goes through the run accumulator
-    const long long glx = (long long)ox + cx0, gly = (long long)oy + cy0;  // low pixel
-    const long long gax = b0 ? glx : glx + 1 - o, gay = b0 ? gly : gly + o;
-    const long long gbx = b0 ? glx + 1 - o : glx, gby = b0 ? gly + o : gly;
+    const int glx = ox + cx0, gly = oy + cy0;  // low pixel
+    const int gax = b0 ? glx : glx + 1 - o, gay = b0 ? gly : gly + o;
+    const int gbx = b0 ? glx + 1 - o : glx, gby = b0 ? gly + o : gly;
     const unsigned long long va = b0 ? vlow : MM_FIX_ONE - vlow;
     if (va && gax >= 0 && gax < M.npix && gay >= 0 && gay < M.npix_y)
-      run_add(M, ra, gay * M.npix + gax, va);
+      run_add(M, ra, (long long)gay * M.npix + gax, va);
     deposit(M, gbx, gby, MM_FIX_ONE - va);
     cnt.line++;
     return TRI_DONE;
   }
   // restrict to the map: frame columns [-ox, npix-1-ox]
-  const long long mcl = -(long long)ox, mch = (long long)M.npix - 1 - ox;
-  const long long mrl = -(long long)oy, mrh = (long long)M.npix_y - 1 - oy;
-  const long long cl = cx0 > mcl ? cx0 : mcl, ch = cx1 < mch ? cx1 : mch;
-  const long long rl = cy0 > mrl ? cy0 : mrl, rh = cy1 < mrh ? cy1 : mrh;
+  const int mcl = -ox, mch = M.npix - 1 - ox;
+  const int mrl = -oy, mrh = M.npix_y - 1 - oy;
+  const int cl = cx0 > mcl ? cx0 : mcl, ch = cx1 < mch ? cx1 : mch;
+  const int rl = cy0 > mrl ? cy0 : mrl, rh = cy1 < mrh ? cy1 : mrh;
   if (cl > ch || rl > rh) return TRI_DONE;  // misses the map
   cnt.clipped++;
   if (cx1 - cx0 <= 1 && cy1 - cy0 <= 1) {
@@ -453,7 +454,7 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
 #pragma unroll
   for (int e = 0; e < 3; e++)
     job.k[e] = (t[(2 * e + 2) % 6] - t[2 * e]) / (t[(2 * e + 3) % 6] - t[2 * e + 1]);
-  if ((ch - cl + 1) * (rh - rl + 1) <= MM_MED_PIXELS)
+  if ((long long)(ch - cl + 1) * (rh - rl + 1) <= MM_MED_PIXELS)
     cnt.strip++;
   else
     cnt.big++;

@@ -68,7 +68,7 @@ __device__ __forceinline__ int lookup_leaf_cached(const MapDev &M, int cx, int c
 // Source-plane position of grid point (i + ti, j + tj) in pixel units:
 // returns the integer pixel and the fraction.  ti = tj = 0 for ray vertices.
 template <bool SQUARE, bool FRAC>
-__device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i, int64_t j,
+__device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int i, int j,
                                            float ti, float tj, bool valid) {
   const int4 *rp = reinterpret_cast<const int4 *>(M.leaf + (leaf < 0 ? 0 : leaf));
   int4 q0 = __ldg(rp), q1 = __ldg(rp + 1), q2 = __ldg(rp + 2), q3 = __ldg(rp + 3);
@@ -82,7 +82,7 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
 
   // vertex position relative to the reference vertex, in grid units (exact
   // integers), and relative to the leaf centre
-  const float fi = (float)(int)(i - i_ref), fj = (float)(int)(j - j_ref);
+  const float fi = (float)(i - i_ref), fj = (float)(j - j_ref);
   float gx = fi - fcx, gy = fj - fcy;
   if (FRAC) {
     gx += ti;
@@ -192,7 +192,7 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int64_t i,
 // culling radius of every direct star (a star above is approached by one
 // row per row; one below or level only recedes).
 template <bool SQUARE>
-__device__ __forceinline__ int vertex_cull_side(const MapDev &M, int leaf, int64_t i, int64_t j,
+__device__ __forceinline__ int vertex_cull_side(const MapDev &M, int leaf, int i, int j,
                                                 int &run) {
   run = 0;
   if (leaf < 0) return MM_CULL_NONE;
@@ -201,7 +201,7 @@ __device__ __forceinline__ int vertex_cull_side(const MapDev &M, int leaf, int64
   if (q3.z == MM_CULL_NONE) return MM_CULL_NONE;
   const int4 q0 = __ldg(rp), q2 = __ldg(rp + 2);
   const float r2 = __int_as_float(q3.w);
-  const float fi = (float)(int)(i - q0.x), fj = (float)(int)(j - q0.y);
+  const float fi = (float)(i - q0.x), fj = (float)(j - q0.y);
   // rows to the sub-cell's upper edge (centre + half-length, grid units)
   const float top = __int_as_float(q0.w) + 1.0f / __int_as_float(q2.y);
   int n = (int)floorf(fminf(top - fj, 1.0e6f)) - 1;
@@ -225,7 +225,7 @@ __device__ __forceinline__ int vertex_cull_side(const MapDev &M, int leaf, int64
 // (lanes without a vertex agree with anything), and the rows from j on the
 // proof holds for in every lane; MM_CULL_NONE otherwise.
 template <bool SQUARE>
-__device__ __forceinline__ int row_cull_side(const MapDev &M, int leaf, int64_t i, int64_t j,
+__device__ __forceinline__ int row_cull_side(const MapDev &M, int leaf, int i, int j,
                                              bool vvalid, int &run) {
   int r = 1 << 30;
   const int s = vvalid ? vertex_cull_side<SQUARE>(M, leaf, i, j, r) : -1;
@@ -327,13 +327,14 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
     const MapDev &M = BATCH ? SM : M1;
     const int64_t local = (int64_t)w - M.work_begin;
     const int64_t s = local % M.strips, b = (local / M.strips) * M.item_stride;
-    const int64_t i = M.col_begin + s * MM_STRIP + lane;
-    const int64_t jb = M.row_begin + b * M.rows_per_item;
-    int64_t je = jb + M.rows_per_item;
-    if (je > M.row_end) je = M.row_end;
-    const bool vvalid = i <= M.col_end;  // vertex columns [col_begin, col_end]
-    const int cx = __ldg(&M.col_cell[vvalid ? i : M.col_end]);
-    const bool cell_col = (lane < MM_STRIP) && (i < M.col_end);
+    // grid indices fit 32 bits (at most 2^31 - 1 rays per axis)
+    const int i = (int)(M.col_begin + s * MM_STRIP) + lane;
+    const int jb = (int)(M.row_begin + b * M.rows_per_item);
+    const int je = (int)min((int64_t)jb + M.rows_per_item, M.row_end);
+    const int col_end = (int)M.col_end;
+    const bool vvalid = i <= col_end;  // vertex columns [col_begin, col_end]
+    const int cx = __ldg(&M.col_cell[vvalid ? i : col_end]);
+    const bool cell_col = (lane < MM_STRIP) && (i < col_end);
     RunAcc ra = {-1, 0ull};
     Vtx prev, prev_r;  // this lane's vertex of the previous row and its right neighbour's
     // culling state of the previous row (warp-uniform): the map edge it is
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
     // one pass more than there are cell rows: the last one maps nothing and
     // shares out what is left in the queue of larger triangles
     int c_gy = INT_MIN, c_leaf = -1;  // lookup cache of this lane's column
-    for (int64_t j = jb + 1;; j++) {
+    for (int j = jb + 1;; j++) {
       const bool fin = j > je;  // warp-uniform
       Vtx cur = prev, cur_r = prev_r;
       int side = MM_CULL_NONE;
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
             // rows j .. j + run - 1 and the one below lie beyond the same map
             // edge: the cells between them map nothing, and none of those
             // rows is computed
-            const int64_t skip = min((int64_t)run, je - j + 1);
+            const int skip = min(run, je - j + 1);
             prev_exact = false;
             if (lane == 0) cnt.culled += (unsigned)skip;
             j += skip - 1;
@@ -453,21 +454,22 @@ __global__ void __launch_bounds__(256, MM_IRS_MINB)
     if ((int64_t)w >= total_work) break;
     const int64_t local = (int64_t)w - M.work_begin;
     const int64_t s = local % M.strips, b = (local / M.strips) * M.item_stride;
-    const int64_t i = M.col_begin + s * MM_STRIP + lane;
-    const int64_t jb = M.row_begin + b * M.rows_per_item;
-    const int64_t je = min(jb + (int64_t)M.rows_per_item, M.row_end);
-    const int64_t jl = je == M.row_end ? je : je - 1;  // last vertex row owned
-    const bool vvalid = i <= M.col_end;
-    const bool owner = vvalid && (lane < MM_STRIP || i == M.col_end);
-    const int cx = __ldg(&M.col_cell[vvalid ? i : M.col_end]);
+    const int i = (int)(M.col_begin + s * MM_STRIP) + lane;
+    const int jb = (int)(M.row_begin + b * M.rows_per_item);
+    const int je = (int)min((int64_t)jb + M.rows_per_item, M.row_end);
+    const int jl = je == (int)M.row_end ? je : je - 1;  // last vertex row owned
+    const int col_end = (int)M.col_end;
+    const bool vvalid = i <= col_end;
+    const bool owner = vvalid && (lane < MM_STRIP || i == col_end);
+    const int cx = __ldg(&M.col_cell[vvalid ? i : col_end]);
     RunAcc ra = {-1, 0ull};
-    for (int64_t j = jb; j <= jl; j++) {
+    for (int j = jb; j <= jl; j++) {
       const int leaf = lookup_leaf(M, cx, __ldg(&M.row_cell[j]));
       if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
       if (M.cull) {
         int run;
         if (row_cull_side<SQUARE>(M, leaf, i, j, vvalid, run) != MM_CULL_NONE) {
-          const int64_t skip = min((int64_t)run, jl - j + 1);
+          const int skip = min(run, jl - j + 1);
           if (lane == 0) cnt.culled += (unsigned)skip;
           j += skip - 1;
           continue;
@@ -586,7 +588,7 @@ __global__ void k_probe(const MapDev *maps, int64_t n, const double *z, double *
   int cx = (int)fmin(fmax(cxd, 0.0), (double)((1 << MM_DMAX) - 1));
   int cy = (int)fmin(fmax(cyd, 0.0), (double)((1 << MM_DMAX) - 1));
   int leaf = ok ? lookup_leaf(M, cx, cy) : -1;
-  Vtx v = shoot_point<SQUARE, true>(M, leaf, i, j, ti, tj, ok && leaf >= 0);
+  Vtx v = shoot_point<SQUARE, true>(M, leaf, (int)i, (int)j, ti, tj, ok && leaf >= 0);
   if (!ok) return;
   if (v.px == MM_VTX_INVALID) {
     w[2 * t] = nan("");
