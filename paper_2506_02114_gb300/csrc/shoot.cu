@@ -51,18 +51,26 @@ __device__ __forceinline__ int lookup_leaf(const MapDev &M, int cx, int cy) {
 // that grid row (the lane's column is fixed), so consecutive vertex rows
 // skip the grid read until they leave it
 __device__ __forceinline__ int lookup_leaf_cached(const MapDev &M, int cx, int cy, int &c_gy,
-                                                  int &c_leaf) {
+                                                  int &c_leaf, bool &c_cull) {
   const int gy = (cy >> M.gshift) - M.gy0;
   if (gy == c_gy) return c_leaf;
   const int gx = (cx >> M.gshift) - M.gx0;
-  if (gx < 0 || gy < 0 || gx >= M.gw || gy >= M.gh) return -1;
-  const int e = __ldg(&M.grid[(int64_t)gy * M.gw + gx]);
-  if (e >= 0) {
-    c_gy = gy;
-    c_leaf = e;
-    return e;
+  int e = -1;
+  if (gx >= 0 && gy >= 0 && gx < M.gw && gy < M.gh) {
+    e = __ldg(&M.grid[(int64_t)gy * M.gw + gx]);
+    if (e >= 0) {
+      c_gy = gy;
+      c_leaf = e;
+    } else {
+      c_gy = INT_MIN;  // a tree walk: not cached
+      e = lookup_leaf(M, cx, cy);
+    }
+  } else {
+    c_gy = INT_MIN;
   }
-  return lookup_leaf(M, cx, cy);
+  // whether the record can prove a vertex beyond the map at all
+  c_cull = e >= 0 && __ldg(&M.leaf[e].cull_side) != MM_CULL_NONE;
+  return e;
 }
 
 // Source-plane position of grid point (i + ti, j + tj) in pixel units:
@@ -352,17 +360,21 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
     // one pass more than there are cell rows: the last one maps nothing and
     // shares out what is left in the queue of larger triangles
     int c_gy = INT_MIN, c_leaf = -1;  // lookup cache of this lane's column
+    bool c_cull = false;              // the cached record has a culling bound
     for (int j = jb + 1;; j++) {
       const bool fin = j > je;  // warp-uniform
       Vtx cur = prev, cur_r = prev_r;
       int side = MM_CULL_NONE;
       if (!fin) {
         const int cy = __ldg(&M.row_cell[j]);
-        const int leaf = lookup_leaf_cached(M, cx, cy, c_gy, c_leaf);
+        const int leaf = lookup_leaf_cached(M, cx, cy, c_gy, c_leaf, c_cull);
         if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
+        // a row is provably beyond the map only if every lane's record has a
+        // culling bound; otherwise the per-vertex test cannot succeed
         if (M.cull) {
-          int run;
-          side = row_cull_side<SQUARE>(M, leaf, i, j, vvalid, run);
+          int run = 0;
+          if (!__any_sync(0xffffffffu, vvalid && !c_cull))
+            side = row_cull_side<SQUARE>(M, leaf, i, j, vvalid, run);
           if (side != MM_CULL_NONE && side == prev_side) {
             // rows j .. j + run - 1 and the one below lie beyond the same map
             // edge: the cells between them map nothing, and none of those
