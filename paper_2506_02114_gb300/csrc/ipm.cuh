@@ -344,11 +344,12 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
     cnt.dropped++;
     return TRI_DONE;
   }
-  // wholly beyond one edge of the map (most triangles of a shooting region):
-  // integer tests on the vertices' pixels, before any arithmetic
-  if (max(a.px, max(b.px, c.px)) < 0 || min(a.px, min(b.px, c.px)) >= M.npix ||
-      max(a.py, max(b.py, c.py)) < 0 || min(a.py, min(b.py, c.py)) >= M.npix_y)
-    return TRI_DONE;
+  // the pixel box from the vertices' pixels (a vertex's pixel is the floor
+  // of its coordinate), and wholly beyond one edge of the map (most
+  // triangles of a shooting region): integer tests before any arithmetic
+  const int xlo = min(a.px, min(b.px, c.px)), xhi = max(a.px, max(b.px, c.px));
+  const int ylo = min(a.py, min(b.py, c.py)), yhi = max(a.py, max(b.py, c.py));
+  if (xhi < 0 || xlo >= M.npix || yhi < 0 || ylo >= M.npix_y) return TRI_DONE;
   const int ox = a.px, oy = a.py;
   float t[6];
   t[0] = a.fx;
@@ -365,24 +366,13 @@ __device__ __forceinline__ int ipm_triangle(const MapDev &M, const Vtx &a,
   }
   // near-critical: local |mu| = image area / source area above the threshold
   cnt.critical += fabsf(area2) < M.crit_area2;
-  if (a.px == b.px && a.px == c.px && a.py == b.py && a.py == c.py) {
+  if (xlo == xhi && ylo == yhi) {
     // all three vertices in one (closed) map pixel: all of the area is there
     run_add(M, ra, (long long)oy * M.npix + ox, MM_FIX_ONE);
     return TRI_DONE;
   }
-  const float xmin = fminf(t[0], fminf(t[2], t[4])), xmax = fmaxf(t[0], fmaxf(t[2], t[4]));
-  const float ymin = fminf(t[1], fminf(t[3], t[5])), ymax = fmaxf(t[1], fmaxf(t[3], t[5]));
-  // pixel range in frame coordinates (clamped well inside int range)
-  const float lim = 1.0e9f;
-  const int cx0 = (int)floorf(fmaxf(xmin, -lim)), cx1 = (int)floorf(fminf(xmax, lim));
-  const int cy0 = (int)floorf(fmaxf(ymin, -lim)), cy1 = (int)floorf(fminf(ymax, lim));
-  if (cx0 == cx1 && cy0 == cy1) {
-    // whole triangle inside one pixel
-    const int gx = ox + cx0, gy = oy + cy0;
-    if (gx >= 0 && gx < M.npix && gy >= 0 && gy < M.npix_y)
-      run_add(M, ra, (long long)gy * M.npix + gx, MM_FIX_ONE);
-    return TRI_DONE;
-  }
+  // pixel range in the frame of vertex a
+  const int cx0 = xlo - ox, cx1 = xhi - ox, cy0 = ylo - oy, cy1 = yhi - oy;
   if ((cx1 - cx0) + (cy1 - cy0) == 1) {
     // (two adjacent pixels that passed the test above: at least one is in
     // the map, so the map restriction below is not needed)
