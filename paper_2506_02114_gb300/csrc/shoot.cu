@@ -475,10 +475,12 @@ __global__ void __launch_bounds__(256, MM_IRS_MINB)
     const bool owner = vvalid && (lane < MM_STRIP || i == col_end);
     const int cx = __ldg(&M.col_cell[vvalid ? i : col_end]);
     RunAcc ra = {-1, 0ull};
+    int c_gy = INT_MIN, c_leaf = -1;  // lookup cache of this lane's column
+    bool c_cull = false;              // the cached record has a culling bound
     for (int j = jb; j <= jl; j++) {
-      const int leaf = lookup_leaf(M, cx, __ldg(&M.row_cell[j]));
+      const int leaf = lookup_leaf_cached(M, cx, __ldg(&M.row_cell[j]), c_gy, c_leaf, c_cull);
       if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
-      if (M.cull) {
+      if (M.cull && !__any_sync(0xffffffffu, vvalid && !c_cull)) {
         int run;
         if (row_cull_side<SQUARE>(M, leaf, i, j, vvalid, run) != MM_CULL_NONE) {
           const int skip = min(run, jl - j + 1);
