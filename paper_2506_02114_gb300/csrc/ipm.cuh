@@ -158,11 +158,17 @@ __device__ __forceinline__ float lone_vertex_share(float u0, float u1, float u2,
 }
 
 // Fixed-point share of T on the low side u < L of one grid line it crosses.
+// The line is chosen from the vertices' integer pixels, and a vertex's FP32
+// coordinate in a neighbouring pixel's frame can round onto the line (k + f
+// with f within 2^-24 of 1), leaving no vertex strictly below it: then
+// nothing of T lies below the line (and all of it when none lies above).
 __device__ __forceinline__ unsigned long long low_side_fixed(float u0, float u1, float u2,
                                                              float L) {
+  const int nlow = (u0 < L) + (u1 < L) + (u2 < L);
   bool lone_low;
   const unsigned long long v = frac_to_fixed(lone_vertex_share(u0, u1, u2, L, lone_low));
-  return lone_low ? v : MM_FIX_ONE - v;
+  const unsigned long long low = lone_low ? v : MM_FIX_ONE - v;
+  return nlow == 0 ? 0ull : (nlow == 3 ? MM_FIX_ONE : low);
 }
 
 // Contribution of edge P -> Q to the signed area of T n {x < X, y < Y}
