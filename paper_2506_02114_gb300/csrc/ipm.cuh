@@ -166,9 +166,9 @@ __device__ __forceinline__ unsigned long long low_side_fixed(float u0, float u1,
                                                              float L) {
   const int nlow = (u0 < L) + (u1 < L) + (u2 < L);
   bool lone_low;
-  const unsigned long long v = frac_to_fixed(lone_vertex_share(u0, u1, u2, L, lone_low));
-  const unsigned long long low = lone_low ? v : MM_FIX_ONE - v;
-  return nlow == 0 ? 0ull : (nlow == 3 ? MM_FIX_ONE : low);
+  const float v = lone_vertex_share(u0, u1, u2, L, lone_low);
+  const float low = nlow == 0 ? 0.f : (nlow == 3 ? 1.f : (lone_low ? v : 1.f - v));
+  return frac_to_fixed(low);
 }
 
 // Contribution of edge P -> Q to the signed area of T n {x < X, y < Y}
