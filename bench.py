@@ -425,10 +425,11 @@ def make_tune_cache(args):
 
 def create_handles(mm, specs, name, args, tune_cache, **extra):
     if name == SWEEP:
-        # a 2^20-slot second-pass queue per map (48 MB); in a batch, batches
-        # that do not fit are dealt by the first pass
+        # each map's second-pass queue holds the larger triangles its tune
+        # record counted, plus a quarter (the library's default); in a
+        # batch, batches that do not fit are dealt by the first pass
         return [mm.create(*sp.args(), fmm_order=sp.fmm_order, autotune=True,
-                          tune_cache=tune_cache, big_queue_slots=1 << 20, **extra)
+                          tune_cache=tune_cache, **extra)
                 for sp in specs]
     sp = specs[0]
     return [mm.create(*sp.args(), fmm_order=sp.fmm_order, autotune=args.autotune,
@@ -722,6 +723,11 @@ def run_native(args):
         order = sorted(range(len(specs)), key=lambda i: len(specs[i].m))
         picks = sorted({order[0], order[len(order) // 2], order[-1]})
         pps, bands, worst = plain_and_error(mm, specs, hs, stats, stream, picks)
+        # the timed handles' device memory (the queues of a sweep hold ~100
+        # GB) goes back to the pool before the end-to-end leg creates its own
+        for h in hs:
+            mm.destroy(h)
+        hs = []
         ppr = pairs_per_ray(specs, [st["rays"] for st in stats])
         # the direct sum's inner loop issues 11 FP64 instructions per star-ray
         # pair (2 subtractions, a multiply and an FMA for |d|^2, the two
@@ -777,6 +783,7 @@ def run_native(args):
                    "sub_levels": sorted({st["sub_levels"] for st in stats}),
                    "rows_per_item": sorted({st["rows_per_item"] for st in stats}),
                    "tuned_from_cache": tuned.count(2), "tuned_by_timing": tuned.count(1),
+                   "queue_gb": sum(st["queue_slots"] for st in stats) * 48 / 1e9,
                    "mapping": "irs" if args.irs else "ipm",
                    "band_rows": list(band[:2]) if band else None,
                    "l2": "flushed before every step (256 MiB write)",

@@ -103,16 +103,20 @@ typedef struct {
                                as the row below (the map is unchanged: such
                                cells lie wholly outside it) */
   int32_t big_queue_slots;  /* queue for the second mapping pass, in triangles:
-                               0 -> 1 per 12 cells (2^16 .. 2^27) when the
-                               map's accumulators (16 B per pixel) fit half
-                               the GPU's L2, else none; -1 -> none (the first
-                               pass deals every larger triangle); n > 0 -> n.
-                               With a queue and a map that fits, the first
-                               pass runs in consecutive segments of work
-                               items, each followed by the second pass, so
-                               that about one larger triangle per 12 cells
-                               fits.  Batches that still do not fit are dealt
-                               by the first pass (same map). */
+                               0 -> when the map's accumulators (16 B per
+                               pixel) fit half the GPU's L2, the larger
+                               triangles the autotuner counted (its
+                               jobs_per_mcell, scaled to the grid) plus a
+                               quarter, else 1 per 12 cells, within 2^16 ..
+                               2^27 (2^20, then none, when the device has not
+                               that much memory free); else none.  -1 -> none
+                               (the first pass deals every larger triangle);
+                               n > 0 -> n.  With a queue and a map that fits,
+                               the first pass runs in consecutive segments of
+                               work items, each followed by the second pass,
+                               so that the expected larger triangles fit.
+                               Batches that still do not fit are dealt by the
+                               first pass (same map). */
   int32_t autotune;         /* FMM mode, 1: mm_create first times candidate
                                settings and keeps the fastest: leaf_size in
                                {16, 32, 64} when its argument is 0, sub_levels in
@@ -133,7 +137,10 @@ typedef struct {
                                choices (NULL: none), read first and appended
                                to after a timed choice.  One object per line:
                                {"key": K, "leaf_size": L, "sub_levels": S,
-                               "rows_per_item": R, "ms_estimate": T}, K built
+                               "rows_per_item": R, "jobs_per_mcell": J,
+                               "ms_estimate": T} (J: larger triangles per 2^20
+                               cells counted by the chosen candidate's sampled
+                               run, -1 or absent when not known), K built
                                from the GPU's compute capability, the requested
                                fmm_order, leaf_size, sub_levels and
                                rows_per_item, and floor(log2) of N_star, the
@@ -231,7 +238,8 @@ typedef struct {
                                4 a star-rectangle corner near a sub-cell, 8 a
                                map index out of range (only the MM_DEBUG build
                                checks, and skips the access) */
-  int32_t reserved2;
+  int32_t queue_slots;      /* capacity of the second-pass queue, in triangles
+                               (0: none; see mm_options.big_queue_slots) */
 } mm_stats;
 
 /*

@@ -85,7 +85,7 @@ class Stats(ctypes.Structure):
                 ("ms_first_pass", ctypes.c_double), ("ms_second_pass", ctypes.c_double),
                 ("rows_per_item", ctypes.c_int32), ("autotuned", ctypes.c_int32),
                 ("ms_autotune", ctypes.c_double), ("triangles_near_critical", ctypes.c_int64),
-                ("error_bits", ctypes.c_uint32), ("reserved2", ctypes.c_int32)]
+                ("error_bits", ctypes.c_uint32), ("queue_slots", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "params"}

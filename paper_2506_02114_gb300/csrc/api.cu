@@ -232,13 +232,16 @@ struct mm_map {
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool ev_recorded = false;
 
-  // autotuner outcome (mm_stats.autotuned, ms_autotune)
+  // autotuner outcome (mm_stats.autotuned, ms_autotune) and the larger
+  // triangles per 2^20 cells its sampled runs counted (-1: not measured),
+  // which sizes the default second-pass queue
   int tuned = 0;
   double ms_tune = 0.0;
+  int32_t jobs_pm = -1;
 
   // The first mapping pass runs in `segments` launches over consecutive work
   // items, each followed by the second pass, so that the queue of larger
-  // triangles (about one per 12 cells) fits its capacity.  Per segment k,
+  // triangles (est_jobs) fits its capacity.  Per segment k,
   // seg_ev[2k] marks the end of its first pass and seg_ev[2k + 1] the end of
   // its second (time_stages only).
   int64_t segments = 1, last_segments = 0;
@@ -751,6 +754,13 @@ static double map_scale(const mm_map *h) {
   return std::ldexp(0.5 * P.h[0] * P.h[1] / (P.delta * P.delta), -32);
 }
 
+// Larger triangles (queued for the second pass) expected from `cells` cells:
+// the autotuner's count scaled to them, else one per 12 cells.
+static int64_t est_jobs(const mm_map *h, int64_t cells) {
+  if (h->jobs_pm >= 0) return (int64_t)std::ceil((double)cells * h->jobs_pm / 1048576.0);
+  return cells / 12;
+}
+
 static mm_status alloc_map_buffers(mm_map *h) {
   const size_t np = (size_t)h->P.npix * h->P.npix_y;
   CK(h->acc.ensure(np));
@@ -764,27 +774,44 @@ static mm_status alloc_map_buffers(mm_map *h) {
   // the second pass reaches a triangle, whereas the first pass deals it where
   // the lines are hot (measured on 5000^2 and 10000^2 maps: no queue was 18 %
   // and 8 % faster than a queue, and first passes split into segments to fit
-  // the queue were 17-44 % slower).  Default: 1 slot per 12 cells, 2^16 ..
-  // 2^27 slots (48 B each), for maps that fit half the L2, else none.
-  // Batches that do not fit are dealt out by the first kernel.
+  // the queue were 17-44 % slower).  Default, for maps that fit half the L2
+  // (else none): the larger triangles the autotuner's sampled runs counted,
+  // with a quarter to spare, else 1 slot per 12 cells; 2^16 .. 2^27 slots
+  // (48 B each).  When that much device memory is not to be had, 2^20 slots,
+  // then none.  Batches that do not fit are dealt out by the first kernel.
   {
     const int64_t cells = (h->col_hi - h->col_lo) * (h->row_hi - h->row_lo);
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
     const bool fits_l2 = 16.0 * (double)h->P.npix * (double)h->P.npix_y <= 0.5 * (double)l2;
     const int32_t want = h->mode == MM_FMM_IRS ? -1 : h->opt.big_queue_slots;
+    const int64_t est = est_jobs(h, cells);
+    const int64_t slots = h->jobs_pm >= 0 ? est + est / 4 + 4096 : est;
     h->bigq_cap = want < 0 ? 0
                   : want > 0 ? (int64_t)want
                   : fits_l2  ? std::min<int64_t>(int64_t(1) << 27,
-                                                 std::max<int64_t>(int64_t(1) << 16, cells / 12))
+                                                 std::max<int64_t>(int64_t(1) << 16, slots))
                              : 0;
-    if (h->bigq_cap > 0) CK(h->bigq.ensure((size_t)h->bigq_cap * MM_TRIJOB_BYTES));
+    if (h->bigq_cap > 0) {
+      cudaError_t e = h->bigq.ensure((size_t)h->bigq_cap * MM_TRIJOB_BYTES);
+      if (e == cudaErrorMemoryAllocation && want == 0) {
+        cudaGetLastError();  // (clears the failed allocation's error)
+        h->bigq_cap = std::min<int64_t>(h->bigq_cap, int64_t(1) << 20);
+        e = h->bigq.ensure((size_t)h->bigq_cap * MM_TRIJOB_BYTES);
+        if (e == cudaErrorMemoryAllocation) {
+          cudaGetLastError();
+          h->bigq_cap = 0;
+          e = cudaSuccess;
+        }
+      }
+      CK(e);
+    }
     CK(h->bigq_n.ensure(2));
     // a map that fits: the first pass runs in segments so that each
-    // segment's larger triangles (about one per 12 cells) fit the queue
+    // segment's larger triangles fit the queue
     h->segments = 1;
     if (h->bigq_cap > 0 && h->mode == MM_FMM_FP32 && fits_l2)
-      h->segments = std::max<int64_t>(1, (cells / 12 + h->bigq_cap - 1) / h->bigq_cap);
+      h->segments = std::max<int64_t>(1, (est + h->bigq_cap - 1) / h->bigq_cap);
     if (h->opt.time_stages && (int64_t)h->seg_ev.size() < 2 * h->segments) {
       const size_t have = h->seg_ev.size();
       h->seg_ev.resize(2 * h->segments, nullptr);
@@ -829,11 +856,11 @@ static MapDev restrict_mapdev(const mm_map *h, const CellRect &r) {
   return m;
 }
 
-// First-pass segments for `cells` cells: about one larger triangle per 12
-// cells must fit the queue (maps that fit L2, polygon mapping only).
+// First-pass segments for `cells` cells: their larger triangles must fit
+// the queue (maps that fit L2, polygon mapping only).
 static int64_t segments_for(const mm_map *h, int64_t cells) {
   if (h->segments <= 1 || h->bigq_cap <= 0) return 1;
-  return std::max<int64_t>(1, (cells / 12 + h->bigq_cap - 1) / h->bigq_cap);
+  return std::max<int64_t>(1, (est_jobs(h, cells) + h->bigq_cap - 1) / h->bigq_cap);
 }
 
 // One run of the handle's map over its cells, or over the rectangle `rect`
@@ -1105,13 +1132,15 @@ static mm_status create_impl(mm_map *h, double kappa_tot, double shear, double s
 // computes (beyond the FMM tolerances), chosen by timing candidate plans.
 // ---------------------------------------------------------------------------
 
+// jobs_pm: the larger triangles per 2^20 cells that the chosen candidate's
+// sampled run counted (-1: none recorded), for the second-pass queue's size
 struct TuneChoice {
-  int32_t leaf = 32, sub = 0, rpi = 0;
+  int32_t leaf = 32, sub = 0, rpi = 0, jobs_pm = -1;
 };
 
 static bool tune_valid(const TuneChoice &c) {
   return c.leaf >= 1 && c.leaf <= 1024 && c.sub >= -1 && c.sub <= MM_SUB_MAX && c.rpi >= 0 &&
-         c.rpi <= 4096;
+         c.rpi <= 4096 && c.jobs_pm >= -1 && c.jobs_pm <= (1 << 21);
 }
 
 static int log2_bucket(double v) { return v >= 1.0 ? (int)std::floor(std::log2(v)) : 0; }
@@ -1155,6 +1184,7 @@ static bool tune_cache_lookup(const char *path, const std::string &key, TuneChoi
     const std::string line(buf);
     if (line.find(want) == std::string::npos) continue;
     TuneChoice c;
+    if (!json_int(line, "jobs_per_mcell", c.jobs_pm)) c.jobs_pm = -1;  // (older lines)
     if (json_int(line, "leaf_size", c.leaf) && json_int(line, "sub_levels", c.sub) &&
         json_int(line, "rows_per_item", c.rpi) && tune_valid(c)) {
       out = c;
@@ -1172,8 +1202,8 @@ static void tune_cache_store(const char *path, const std::string &key, const Tun
   if (!f) return;
   fprintf(f,
           "{\"key\": \"%s\", \"leaf_size\": %d, \"sub_levels\": %d, \"rows_per_item\": %d, "
-          "\"ms_estimate\": %.4f}\n",
-          key.c_str(), c.leaf, c.sub, c.rpi, ms);
+          "\"jobs_per_mcell\": %d, \"ms_estimate\": %.4f}\n",
+          key.c_str(), c.leaf, c.sub, c.rpi, c.jobs_pm, ms);
   fclose(f);
 }
 
@@ -1204,11 +1234,13 @@ static mm_status trial_ms(mm_map *t, double scale, double &ms) {
 }
 
 // Times every candidate (leaf_size x sub_levels x rows_per_item over the
-// settings left 0) and writes the fastest into o / leaf_size.
+// settings left 0) and writes the fastest into o / leaf_size, and the
+// larger triangles per 2^20 cells its sampled run counted into jobs_pm.
 static mm_status autotune(const CreateArgs &a, mm_options &o, int32_t &leaf_size, int &tuned,
-                          double &ms_tune) {
+                          double &ms_tune, int32_t &jobs_pm) {
   tuned = 0;
   ms_tune = 0.0;
+  jobs_pm = -1;
   if (!o.autotune || o.mode != MM_FMM_FP32) return MM_OK;
   const auto t0 = std::chrono::steady_clock::now();
   std::vector<int32_t> leafs = {leaf_size}, subs = {o.sub_levels}, rpis = {o.rows_per_item};
@@ -1270,6 +1302,18 @@ static mm_status autotune(const CreateArgs &a, mm_options &o, int32_t &leaf_size
             best.sub = sub;
             best.rpi = rpis[r];
             any = true;
+            // the larger triangles of the sampled run (statistics 3 and 4),
+            // scaled to the whole grid, per 2^20 cells
+            unsigned long long st[8] = {};
+            ce = cudaMemcpy(st, t->stat.p, sizeof st, cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) {
+              s = fail(MM_ECUDA, "autotune: %s", cudaGetErrorString(ce));
+              break;
+            }
+            const double cells = (double)(t->col_hi - t->col_lo) * (double)(t->row_hi - t->row_lo);
+            const double pm = cells > 0.0 ? (double)(st[3] + st[4]) * scale * 1048576.0 / cells
+                                          : 0.0;
+            best.jobs_pm = (int32_t)std::min(std::ceil(pm), (double)(1 << 21));
           }
         }
         if (s != MM_OK) {
@@ -1293,6 +1337,7 @@ static mm_status autotune(const CreateArgs &a, mm_options &o, int32_t &leaf_size
   leaf_size = best.leaf;
   o.sub_levels = best.sub;
   o.rows_per_item = best.rpi;
+  jobs_pm = best.jobs_pm;
   ms_tune = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                 .count();
   return MM_OK;
@@ -1314,7 +1359,8 @@ mm_status mm_create(double kappa_tot, double shear, double smooth_fraction, int6
                           fmm_order > MM_PMAX || h->opt.sub_levels < -1 ||
                           h->opt.sub_levels > MM_SUB_MAX))
     h->opt.autotune = 0;  // create_impl reports the invalid argument
-  if (h->opt.autotune) s = autotune(args, h->opt, leaf_size, h->tuned, h->ms_tune);
+  if (h->opt.autotune)
+    s = autotune(args, h->opt, leaf_size, h->tuned, h->ms_tune, h->jobs_pm);
   h->opt.autotune = 0;
   h->opt.tune_cache = nullptr;
   if (s == MM_OK)
@@ -1573,6 +1619,7 @@ mm_status mm_get_stats(const mm_map *hc, mm_stats *out) {
   out->cells = (h->col_hi - h->col_lo) * (h->row_hi - h->row_lo);
   out->ms_tree = out->ms_expansions = out->ms_shoot = out->ms_normalize = out->ms_total = -1.0;
   out->ms_first_pass = out->ms_second_pass = -1.0;
+  out->queue_slots = (int32_t)std::min<int64_t>(h->bigq_cap, INT32_MAX);
   if (h->last_stream || h->ran) CK(cudaStreamSynchronize(h->last_stream));
   if (h->err.p)
     CK(cudaMemcpy(&out->error_bits, h->err.p, sizeof(unsigned), cudaMemcpyDeviceToHost));

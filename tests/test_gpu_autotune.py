@@ -46,6 +46,16 @@ def choice(st):
     return st["leaf_size"], st["sub_levels"], st["rows_per_item"]
 
 
+def default_queue(cells, jobs_per_mcell):
+    """The default second-pass queue of a map that fits half the L2: the
+    larger triangles the tuner counted, scaled to the grid, plus a quarter
+    (else one per 12 cells), within 2^16 .. 2^27 slots."""
+    if jobs_per_mcell >= 0:
+        est = -(-cells * jobs_per_mcell // 2**20)
+        return min(2**27, max(2**16, est + est // 4 + 4096))
+    return min(2**27, max(2**16, cells // 12))
+
+
 def test_autotune_chooses_caches_and_meets_the_oracle(oracle_mod, tmp_path):
     m, pos, p = field(oracle_mod)
     cache = tmp_path / "tune.jsonl"
@@ -54,6 +64,8 @@ def test_autotune_chooses_caches_and_meets_the_oracle(oracle_mod, tmp_path):
     assert st["autotuned"] == 1 and st["ms_autotune"] > 0.0
     assert st["leaf_size"] in (16, 32, 64) and st["sub_levels"] in (1, 2)
     fixed = fixed_map(h)
+    after = mm.get_stats(h)
+    jobs = after["triangles_box"] + after["triangles_rows"]
     mu = mm.get_map(h)
     mm.destroy(h)
     mu_ref, _ = oracle_mod.magnification_map(p, m, pos)
@@ -65,6 +77,11 @@ def test_autotune_chooses_caches_and_meets_the_oracle(oracle_mod, tmp_path):
     assert rec["key"].startswith("sm_") and rec["ms_estimate"] > 0.0
     assert (rec["leaf_size"], rec["sub_levels"]) == (st["leaf_size"], st["sub_levels"])
     assert rec["rows_per_item"] in (0, 64, 512)
+    # the larger triangles the tuner counted size the handle's queue: at
+    # least the ones this run queued (statistics box + rows), one per slot
+    assert jobs > 0 and rec["jobs_per_mcell"] >= 0
+    assert st["queue_slots"] == default_queue(st["cells"], rec["jobs_per_mcell"])
+    assert st["queue_slots"] >= jobs
 
     # the cached choice is taken without timing, and the map is the same
     h2 = make(m, pos, p, autotune=True, tune_cache=str(cache))
@@ -115,6 +132,8 @@ def test_unusable_cache_lines_are_ignored(oracle_mod, tmp_path):
     st = mm.get_stats(h)
     mm.destroy(h)
     assert st["autotuned"] == 2 and choice(st) == (16, 1, 64)
+    # (a line without jobs_per_mcell: one slot per 12 cells)
+    assert st["queue_slots"] == default_queue(st["cells"], -1)
 
 
 def test_autotuned_handles_batch_like_single_runs(oracle_mod, tmp_path):
