@@ -117,7 +117,9 @@ def parse_args():
                          "and work-item rows (no cache)")
     ap.add_argument("--retune", action="store_true",
                     help="sweep: ignore the shipped tune cache, tune every key and write the "
-                         "cache to gpurun_out/tune_sm_103.jsonl")
+                         "new cache to --tune-out")
+    ap.add_argument("--tune-out", default="tune_sm_103.jsonl",
+                    help="--retune: file the new tune cache is written to")
     a = ap.parse_args()
     if a.irs:
         a.kernel_only = True
@@ -763,8 +765,9 @@ def run_native(args):
     if not (args.no_cpu_baseline or args.kernel_only) and world == 1:
         cpu, _ = cpu_leg(specs, name, args.cpu_seconds, one_core=not args.no_one_core)
     if args.retune:
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        shutil.copyfile(tune_cache, os.path.join(ROOT, "gpurun_out", "tune_sm_103.jsonl"))
+        out_dir = os.path.dirname(os.path.abspath(args.tune_out))
+        os.makedirs(out_dir, exist_ok=True)
+        shutil.copyfile(tune_cache, args.tune_out)
     os.unlink(tune_cache)
 
     tuned = [st["autotuned"] for st in stats]
