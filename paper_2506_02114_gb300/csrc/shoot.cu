@@ -361,6 +361,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
     // shares out what is left in the queue of larger triangles
     int c_gy = INT_MIN, c_leaf = -1;  // lookup cache of this lane's column
     bool c_cull = false;              // the cached record has a culling bound
+    int cull_wait = 0, cull_pause = 0;  // rows left before the next culling test
     for (int j = jb + 1;; j++) {
       const bool fin = j > je;  // warp-uniform
       Vtx cur = prev, cur_r = prev_r;
@@ -373,8 +374,14 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
         // culling bound; otherwise the per-vertex test cannot succeed
         if (M.cull) {
           int run = 0;
-          if (!__any_sync(0xffffffffu, vvalid && !c_cull))
+          if (cull_wait > 0) {
+            cull_wait--;
+          } else if (!__any_sync(0xffffffffu, vvalid && !c_cull)) {
             side = row_cull_side<SQUARE>(M, leaf, i, j, vvalid, run);
+            // a failed test pauses the tests of the next rows (1, 3, ... up to 8)
+            cull_pause = side == MM_CULL_NONE ? min(2 * cull_pause + 1, 8) : 0;
+            cull_wait = cull_pause;
+          }
           if (side != MM_CULL_NONE && side == prev_side) {
             // rows j .. j + run - 1 and the one below lie beyond the same map
             // edge: the cells between them map nothing, and none of those
@@ -477,17 +484,24 @@ __global__ void __launch_bounds__(256, MM_IRS_MINB)
     RunAcc ra = {-1, 0ull};
     int c_gy = INT_MIN, c_leaf = -1;  // lookup cache of this lane's column
     bool c_cull = false;              // the cached record has a culling bound
+    int cull_wait = 0, cull_pause = 0;  // rows left before the next culling test
     for (int j = jb; j <= jl; j++) {
       const int leaf = lookup_leaf_cached(M, cx, __ldg(&M.row_cell[j]), c_gy, c_leaf, c_cull);
       if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
-      if (M.cull && !__any_sync(0xffffffffu, vvalid && !c_cull)) {
+      if (M.cull && cull_wait > 0) {
+        cull_wait--;
+      } else if (M.cull && !__any_sync(0xffffffffu, vvalid && !c_cull)) {
         int run;
         if (row_cull_side<SQUARE>(M, leaf, i, j, vvalid, run) != MM_CULL_NONE) {
           const int skip = min(run, jl - j + 1);
           if (lane == 0) cnt.culled += (unsigned)skip;
           j += skip - 1;
+          cull_pause = 0;
           continue;
         }
+        // a failed test pauses the tests of the next rows (1, 3, ... up to 8)
+        cull_pause = min(2 * cull_pause + 1, 8);
+        cull_wait = cull_pause;
       }
       const Vtx v = shoot_point<SQUARE, false>(M, leaf, i, j, 0.f, 0.f, vvalid);
       if (owner) {
