@@ -73,6 +73,20 @@ __device__ __forceinline__ int lookup_leaf_cached(const MapDev &M, int cx, int c
   return e;
 }
 
+// One Horner step of the two far-field chains: E <- E w + (c.x, c.y) and
+// O <- O w + (c.z, c.w) in complex arithmetic, w = (wx, wy).
+__device__ __forceinline__ void horner_pair(const float4 c, float wx, float wy, float &Er,
+                                            float &Ei, float &Or, float &Oi) {
+  const float er = fmaf(Er, wx, fmaf(-Ei, wy, c.x));
+  const float ei = fmaf(Er, wy, fmaf(Ei, wx, c.y));
+  const float orr = fmaf(Or, wx, fmaf(-Oi, wy, c.z));
+  const float oi = fmaf(Or, wy, fmaf(Oi, wx, c.w));
+  Er = er;
+  Ei = ei;
+  Or = orr;
+  Oi = oi;
+}
+
 // Source-plane position of grid point (i + ti, j + tj) in pixel units:
 // returns the integer pixel and the fraction.  ti = tj = 0 for ray vertices.
 template <bool SQUARE, bool FRAC>
@@ -153,18 +167,29 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int i, int
     const float zx = gx * zsx, zy = gy * zsy;
     const float wx = fmaf(zx, zx, -zy * zy), wy = 2.f * zx * zy;
     const float4 *e = reinterpret_cast<const float4 *>(M.coef + coef_off);
-    float4 c = __ldg(e + (npair - 1));
+    const float4 c = __ldg(e + (npair - 1));
     float Er = c.x, Ei = c.y, Or = c.z, Oi = c.w;
-    for (int j = npair - 2; j >= 0; j--) {
-      c = __ldg(e + j);
-      const float er = fmaf(Er, wx, fmaf(-Ei, wy, c.x));
-      const float ei = fmaf(Er, wy, fmaf(Ei, wx, c.y));
-      const float orr = fmaf(Or, wx, fmaf(-Oi, wy, c.z));
-      const float oi = fmaf(Or, wy, fmaf(Oi, wx, c.w));
-      Er = er;
-      Ei = ei;
-      Or = orr;
-      Oi = oi;
+    if (npair == 7) {
+      // the usual case (15 terms): the other six pairs are all loaded before
+      // the chains start, so their latencies overlap (a loop that loads each
+      // pair where it is used waits on every load in turn)
+      float4 cc[6];
+#pragma unroll
+      for (int j = 0; j < 6; j++) cc[j] = __ldg(e + j);
+#pragma unroll
+      for (int j = 5; j >= 0; j--) horner_pair(cc[j], wx, wy, Er, Ei, Or, Oi);
+    } else {
+      // other orders: four pairs loaded at a time
+      int j = npair - 2;
+      for (; j >= 3; j -= 4) {
+        const float4 c0 = __ldg(e + j), c1 = __ldg(e + j - 1), c2 = __ldg(e + j - 2),
+                     c3 = __ldg(e + j - 3);
+        horner_pair(c0, wx, wy, Er, Ei, Or, Oi);
+        horner_pair(c1, wx, wy, Er, Ei, Or, Oi);
+        horner_pair(c2, wx, wy, Er, Ei, Or, Oi);
+        horner_pair(c3, wx, wy, Er, Ei, Or, Oi);
+      }
+      for (; j >= 0; j--) horner_pair(__ldg(e + j), wx, wy, Er, Ei, Or, Oi);
     }
     fr = fmaf(zx, Er, fmaf(-zy, Ei, fmaf(wx, Or, -wy * Oi)));
     fim = fmaf(zx, Ei, fmaf(zy, Er, fmaf(wx, Oi, wy * Or)));
