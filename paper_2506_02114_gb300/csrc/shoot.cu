@@ -89,7 +89,12 @@ __device__ __forceinline__ void horner_pair(const float4 c, float wx, float wy, 
 
 // Source-plane position of grid point (i + ti, j + tj) in pixel units:
 // returns the integer pixel and the fraction.  ti = tj = 0 for ray vertices.
-template <bool SQUARE, bool FRAC>
+// PRELOAD: the far-field coefficient pairs are loaded ahead of the Horner
+// steps (all six of the usual 15-term case at once, other orders four at a
+// time); else each where it is used, which holds fewer registers across the
+// steps (better in the polygon-mapping kernel of a map without a
+// second-pass queue, which deals every larger triangle itself).
+template <bool SQUARE, bool FRAC, bool PRELOAD = true>
 __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int i, int j,
                                            float ti, float tj, bool valid) {
   const int4 *rp = reinterpret_cast<const int4 *>(M.leaf + (leaf < 0 ? 0 : leaf));
@@ -169,7 +174,9 @@ __device__ __forceinline__ Vtx shoot_point(const MapDev &M, int leaf, int i, int
     const float4 *e = reinterpret_cast<const float4 *>(M.coef + coef_off);
     const float4 c = __ldg(e + (npair - 1));
     float Er = c.x, Ei = c.y, Or = c.z, Oi = c.w;
-    if (npair == 7) {
+    if (!PRELOAD) {
+      for (int j = npair - 2; j >= 0; j--) horner_pair(__ldg(e + j), wx, wy, Er, Ei, Or, Oi);
+    } else if (npair == 7) {
       // the usual case (15 terms): the other six pairs are all loaded before
       // the chains start, so their latencies overlap (a loop that loads each
       // pair where it is used waits on every load in turn)
@@ -311,7 +318,7 @@ __device__ __forceinline__ void flush_counters(const MapDev &M, IpmCounters &cnt
 // A single map (BATCH = false) arrives by value as a launch parameter, so
 // its fields are read from the constant bank instead of held in registers;
 // a batch reads its maps from the device array `maps`.
-template <bool SQUARE, bool BATCH>
+template <bool SQUARE, bool BATCH, bool PRELOAD>
 __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
     k_shoot_ipm(const MapDev *__restrict__ maps, const MapDev M1, int n_maps, int64_t total_work,
                 unsigned long long *work_counter, unsigned *err) {
@@ -377,7 +384,7 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
     {
       const int leaf = lookup_leaf(M, cx, __ldg(&M.row_cell[jb]));
       if (leaf < 0 && vvalid) atomicOr(err, ERR_LOOKUP);
-      prev = shoot_point<SQUARE, false>(M, leaf, i, jb, 0.f, 0.f, vvalid);
+      prev = shoot_point<SQUARE, false, PRELOAD>(M, leaf, i, jb, 0.f, 0.f, vvalid);
       prev_r = shfl_down_vtx(prev, 1);
       int run;
       if (M.cull) prev_side = row_cull_side<SQUARE>(M, leaf, i, jb, vvalid, run);
@@ -420,12 +427,12 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
           if (!prev_exact) {
             // the row below was not computed; its cells with this row are needed
             const int lp = lookup_leaf(M, cx, __ldg(&M.row_cell[j - 1]));
-            prev = shoot_point<SQUARE, false>(M, lp, i, j - 1, 0.f, 0.f, vvalid);
+            prev = shoot_point<SQUARE, false, PRELOAD>(M, lp, i, j - 1, 0.f, 0.f, vvalid);
             prev_r = shfl_down_vtx(prev, 1);
             prev_exact = true;
           }
         }
-        cur = shoot_point<SQUARE, false>(M, leaf, i, j, 0.f, 0.f, vvalid);
+        cur = shoot_point<SQUARE, false, PRELOAD>(M, leaf, i, j, 0.f, 0.f, vvalid);
         cur_r = shfl_down_vtx(cur, 1);
         // a row of cells all beyond the map (and none with a non-finite
         // vertex, which must be counted) has nothing to map
@@ -656,16 +663,16 @@ __global__ void k_probe(const MapDev *maps, int64_t n, const double *z, double *
 // host launchers
 // ---------------------------------------------------------------------------
 
-template <bool SQUARE, bool BATCH>
+template <bool SQUARE, bool BATCH, bool PRELOAD>
 static cudaError_t launch_shoot_t(const MapDev *d_maps, const MapDev &m1, int n_maps,
                                   int64_t total_work, unsigned long long *counter, unsigned *err,
                                   int grid, cudaStream_t st) {
   const int smem = (int)MM_SHOOT_SMEM_BYTES;
-  cudaError_t e = cudaFuncSetAttribute(k_shoot_ipm<SQUARE, BATCH>,
+  cudaError_t e = cudaFuncSetAttribute(k_shoot_ipm<SQUARE, BATCH, PRELOAD>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_shoot_ipm<SQUARE, BATCH><<<grid, 256, smem, st>>>(d_maps, m1, n_maps, total_work, counter,
-                                                      err);
+  k_shoot_ipm<SQUARE, BATCH, PRELOAD><<<grid, 256, smem, st>>>(d_maps, m1, n_maps, total_work,
+                                                               counter, err);
   return cudaGetLastError();
 }
 
@@ -674,16 +681,26 @@ cudaError_t launch_shoot_ipm(const MapDev *d_maps, const MapDev *h_single, int n
                              unsigned *err, int grid, cudaStream_t st) {
   if (total_work <= 0) return cudaSuccess;
   if (n_maps == 1 && h_single) {
-    return square ? launch_shoot_t<true, false>(nullptr, *h_single, 1, total_work, counter, err,
-                                                grid, st)
-                  : launch_shoot_t<false, false>(nullptr, *h_single, 1, total_work, counter,
-                                                 err, grid, st);
+    // a map without a second-pass queue deals every larger triangle in this
+    // kernel, which then runs faster with the far field's loads in place
+    // (3-4 % on 10000^2 and 10000 x 1000 maps); with a queue the loads
+    // ahead win (2-3 %)
+    const MapDev &m = *h_single;
+    if (m.bigq_cap > 0)
+      return square ? launch_shoot_t<true, false, true>(nullptr, m, 1, total_work, counter, err,
+                                                        grid, st)
+                    : launch_shoot_t<false, false, true>(nullptr, m, 1, total_work, counter,
+                                                         err, grid, st);
+    return square ? launch_shoot_t<true, false, false>(nullptr, m, 1, total_work, counter, err,
+                                                       grid, st)
+                  : launch_shoot_t<false, false, false>(nullptr, m, 1, total_work, counter, err,
+                                                        grid, st);
   }
   const MapDev none{};
-  return square ? launch_shoot_t<true, true>(d_maps, none, n_maps, total_work, counter, err, grid,
-                                             st)
-                : launch_shoot_t<false, true>(d_maps, none, n_maps, total_work, counter, err,
-                                              grid, st);
+  return square ? launch_shoot_t<true, true, true>(d_maps, none, n_maps, total_work, counter, err,
+                                                   grid, st)
+                : launch_shoot_t<false, true, true>(d_maps, none, n_maps, total_work, counter,
+                                                    err, grid, st);
 }
 
 // Device-side assembly of a batch's descriptor array from the handles' own
