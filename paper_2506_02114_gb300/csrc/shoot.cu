@@ -551,8 +551,9 @@ __global__ void __launch_bounds__(256, MM_IRS_MINB)
 // Second pass over the larger triangles k_shoot_ipm (or k_ipm_vertices)
 // queued for the map: each warp takes batches of 32 from the device queue
 // and deals out their pixel rows and partially covered pixels
-// (warp_tri_jobs), at 4 blocks per SM where the first kernel runs 2.
-#define MM_BIG_MINB 4
+// (warp_tri_jobs), at 5 blocks per SM where the first kernel runs 2 (48
+// registers allow 5 without spills: 3 % faster than 4; 6 forces spills)
+#define MM_BIG_MINB 5
 __global__ void __launch_bounds__(256, MM_BIG_MINB) k_big_ipm(const MapDev M) {
   __shared__ TriJob q[8][32];
   __shared__ RowRecs rr[8];
