@@ -488,10 +488,11 @@ __global__ void __launch_bounds__(256, MM_SHOOT_MINB)
 // counted once.  Rows proven to land beyond a map edge are skipped: none of
 // their rays can count, and a culled vertex is never non-finite (a ray on a
 // star lies inside that star's culling radius).
-// 3 blocks of 8 warps per SM (80 registers): the deflection alone gains
-// from the occupancy that k_shoot_ipm's mapping code cannot afford (17 %
-// faster than 2 blocks on the benchmark grid).
-#define MM_IRS_MINB 3
+// 4 blocks of 8 warps per SM (64 registers, no spills): the deflection
+// alone gains from the occupancy that k_shoot_ipm's mapping code cannot
+// afford (on the 2000^2 grid 3 blocks were 17 % faster than 2, and 4 are
+// 8 % faster than 3; 5 spill and are slower).
+#define MM_IRS_MINB 4
 template <bool SQUARE>
 __global__ void __launch_bounds__(256, MM_IRS_MINB)
     k_shoot_irs(const MapDev M, int64_t total_work, unsigned long long *work_counter,
