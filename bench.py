@@ -64,12 +64,12 @@ TUNE_CACHE = os.path.join(ROOT, "paper_2506_02114_gb300", "tune", "sm_103.jsonl"
 # (profiles/counters_fmm_fp32_salpeter_2000_rpp1.md): valid only for the kernel
 # sources they were taken on (hash below), reported beside the live roofline.
 NCU_COUNTERS = {
-    "sources_sha1": "c3511adda95a3204e76d439841c5c413762e9069",
+    "sources_sha1": "5517307e56512defd1c015340608c52b0e4ab670",
     "case": "fmm_fp32_salpeter_2000 at 1 ray per pixel (1.64e8 rays), ncu --clock-control none",
-    "k_shoot_ipm": {"issue_active": 0.633, "warps_active": 0.193, "alu_active": 0.504,
-                    "fma_active": 0.191, "l2_red_requests_per_s": 4.06e10},
-    "k_big_ipm": {"issue_active": 0.807, "warps_active": 0.546, "alu_active": 0.630,
-                  "fma_active": 0.300, "l2_red_requests_per_s": 9.61e10},
+    "k_shoot_ipm": {"issue_active": 0.633, "warps_active": 0.194, "alu_active": 0.505,
+                    "fma_active": 0.191, "l2_red_requests_per_s": 4.10e10},
+    "k_big_ipm": {"issue_active": 0.803, "warps_active": 0.548, "alu_active": 0.630,
+                  "fma_active": 0.299, "l2_red_requests_per_s": 9.63e10},
     "k_direct64_vertices": {"fp64_pipe_active": 0.907},
 }
 
